@@ -1,0 +1,137 @@
+/*
+ * fca.h -- C ABI of the GB300 (sm_103a) library for EM parameter estimation of two-source
+ * full-rank spatial covariance analysis (FCA), in two forms:
+ *
+ *   conventional EM   Ito, Araki, Nakatani, "FastFCA" (arXiv 1805.06572), Sec. 2,
+ *                     Eqs. (MMSE), (postquadexp), (vupdate), (Supdate): a frame-wise
+ *                     M x M inverse of v1 S1 + v2 S2 at every time-frequency point;
+ *   FastFCA           Sec. 3 and Algorithm 1: a per-frequency generalised eigenvector
+ *                     basis P (Eq. (GEVD)) jointly diagonalises S1 and S2, so every
+ *                     time-frequency point needs only scalar updates (Eqs. (MMSEtilde),
+ *                     (updatePhitildeeff), (updateveff), (updateStildeeff)) and P is
+ *                     updated once per frequency per iteration (Eqs. (updatePeff),
+ *                     (updateLambdaeff)).
+ *
+ * Model (Sec. 2): y(n,f) = x1(n,f) + x2(n,f) in C^M, x_j ~ CN(0, v_j(n,f) S_j(f)), with N
+ * frames and F frequency bins; both forms maximise the likelihood of Eq. (like).
+ *
+ * Conventions shared by every entry point:
+ *   - Complex numbers are interleaved (re, im). complex64 = two floats, complex128 = two
+ *     doubles. Matrices are row-major. Layouts (C order, last index fastest):
+ *       y, x1, x2   [F][N][M]       complex64 (y may instead be FP16, see fca_problem)
+ *       v           [2][F][N]       source powers v_j(n,f), j = 0 -> source 1
+ *       S           [2][F][M][M]    spatial covariances S_j(f), Hermitian positive definite
+ *   - Every call is asynchronous on the CUDA stream it is given (NULL = legacy default
+ *     stream) unless stated otherwise. Argument errors are detected on the host and
+ *     returned synchronously, before anything is enqueued.
+ *   - Errors found by the GPU (a matrix that is not positive definite, a non-finite value,
+ *     an eigensolver that does not converge) are recorded in a device status word, first
+ *     error wins; fca_sync_status() waits for the stream and returns it. Once a state has
+ *     failed, every later call on it returns FCA_ERR_STATE until fca_load() reloads it.
+ *   - The library owns all EM state on the device (a copy of y, v, the parameters, and
+ *     scratch). The caller owns every pointer it passes; input buffers are only read by
+ *     work enqueued by the call, so they may be reused once that work has completed on the
+ *     stream. Device pointers must be on the current CUDA device.
+ *   - Sizes: 1 <= M <= 8, F >= 1, N >= 1, and F * N * M < 2^31.
+ */
+#ifndef FCA_H_
+#define FCA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fca_state fca_state; /* opaque, allocated by fca_init, freed by fca_free */
+
+typedef enum {
+  FCA_OK = 0,
+  FCA_ERR_ARG = 1,         /* invalid argument (host check)                               */
+  FCA_ERR_CUDA = 2,        /* a CUDA runtime call failed                                  */
+  FCA_ERR_NOMEM = 3,       /* device allocation failed                                    */
+  FCA_ERR_NOT_PD = 4,      /* a covariance that must be positive definite is not          */
+  FCA_ERR_EIG_NOCONV = 5,  /* the Jacobi eigensolver hit its sweep cap                    */
+  FCA_ERR_NONFINITE = 6,   /* a NaN or infinity appeared in v, S, P or the log-likelihood */
+  FCA_ERR_TIMEOUT = 7,     /* a bounded device wait ran out                               */
+  FCA_ERR_STATE = 8        /* the state failed earlier, or the call does not fit its form */
+} fca_status;
+
+enum { FCA_STORE_C64 = 0, FCA_STORE_F16_SCALED = 1 };
+enum { FCA_MEM_DEVICE = 0, FCA_MEM_HOST = 1 };
+enum { FCA_SEP_ALG1 = 0, FCA_SEP_FINAL_PARAMS = 1 };
+
+/*
+ * One mixture and its initial parameters (Algorithm 1, first step: "set initial values").
+ *   storage = FCA_STORE_C64:         y is complex64 [F][N][M].
+ *   storage = FCA_STORE_F16_SCALED:  y is FP16 pairs [F][N][M][2] holding g_f * y(n,f), and
+ *                                    y_scale[f] = g_f > 0 (float [F]); the EM runs on the
+ *                                    decoded mixture y16 / g_f.
+ *   v0:  double [2][F][N], initial v_j^(0)(n,f) > 0 (clamped to the positivity floor).
+ *   S0:  complex128 [2][F][M][M], initial S_j^(0)(f), Hermitian positive definite.
+ *   location: FCA_MEM_DEVICE or FCA_MEM_HOST, for all of y, y_scale, v0 and S0. Host
+ *   buffers are copied with cudaMemcpyAsync; pinned host memory makes that asynchronous.
+ */
+typedef struct {
+  int32_t M, F, N;
+  int32_t storage;
+  int32_t location;
+  const void* y;
+  const float* y_scale;
+  const double* v0;
+  const double* S0;
+} fca_problem;
+
+/* Allocate a state for the shapes in *p and load it (as fca_load). On success *out owns the
+ * state; on failure *out is NULL and nothing stays allocated. */
+fca_status fca_init(const fca_problem* p, void* cuda_stream, fca_state** out);
+
+/* Reload a state with a new mixture and initial parameters of the same M, F, N and storage.
+ * Clears a failed status. The positivity floor of v is recomputed from the new y:
+ * vfloor(f) = max(1e-12 * mean_{n,m} |y_m(n,f)|^2, 1e-30) (applied after every v update). */
+fca_status fca_load(fca_state* s, const fca_problem* p, void* cuda_stream);
+
+/* Run `iters` >= 0 iterations of conventional EM (Sec. 2, Eqs. (MMSE)-(Supdate)).
+ * If the state's parameters are in the FastFCA form (P, Lambda), they are first converted
+ * to S_j = P^-H T_j P^-1 (Eqs. (Sdiag), (recoverS)).
+ * loglik_dev: NULL or device double [iters]; entry l receives log of Eq. (like) at the
+ * parameters of iteration l (before that iteration's update), summed over all n and f. */
+fca_status fca_em_conventional(fca_state* s, int32_t iters, double* loglik_dev, void* cuda_stream);
+
+/* Run `iters` >= 0 iterations of FastFCA (Algorithm 1, steps 2-10). If the parameters are in
+ * the conventional form (S1, S2), P and Lambda are first obtained from the generalised
+ * eigenproblem of (S1, S2) (Eq. (GEVD)). loglik_dev as for fca_em_conventional. */
+fca_status fca_em_fast(fca_state* s, int32_t iters, double* loglik_dev, void* cuda_stream);
+
+/* Posterior means (MMSE source images, Eq. (MMSE); Algorithm 1, last step) into caller-owned
+ * device buffers x1_dev, x2_dev, complex64 [F][N][M].
+ *   mode FCA_SEP_ALG1:         the E-step of the last iteration run, i.e. the parameters of
+ *                              iteration L-1 (the initial parameters if no iteration ran);
+ *   mode FCA_SEP_FINAL_PARAMS: one more E-step with the current parameters.
+ * The FastFCA form returns mu1 = P^-H mut1 and mu2 = y - mu1 (y = x1 + x2, Sec. 2); the
+ * conventional form returns mu_j = v_j S_j (v1 S1 + v2 S2)^-1 y for j = 1, 2. */
+fca_status fca_separate(fca_state* s, void* x1_dev, void* x2_dev, int32_t mode, void* cuda_stream);
+
+/* Current parameters. v_dev: NULL or device float [2][F][N] (enqueued copy). S_host: NULL or
+ * host complex128 [2][F][M][M]; when given, the call synchronises the stream (S is formed
+ * on the device from (P, Lambda) in the FastFCA form, Eqs. (Sdiag), (recoverS)). */
+fca_status fca_get_params(fca_state* s, float* v_dev, double* S_host, void* cuda_stream);
+
+/* Synchronise the stream and return the first device-side error of this state (FCA_OK if
+ * none). */
+fca_status fca_sync_status(fca_state* s, void* cuda_stream);
+
+/* Release the state and all its device memory. Synchronises the device first. NULL is a
+ * no-op. */
+void fca_free(fca_state* s);
+
+/* Static description of a status code. */
+const char* fca_status_string(fca_status st);
+
+/* Library build identifier (compile-time target and version). */
+const char* fca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCA_H_ */

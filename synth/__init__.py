@@ -1,0 +1,113 @@
+"""Seeded synthetic inputs for two-source FCA (shared by the oracle tests, the GPU
+tests and the benchmark).
+
+This module holds no step of the EM method. It draws mixtures from the generative
+model the paper assumes (Sec. 2: y = x1 + x2, x_j ~ CN(0, v_j S_j), Eq. (fullrank)),
+builds the initial parameters (Algorithm 1 leaves the initial values to the user) and
+optionally encodes the mixture as FP16 with a per-frequency scale.
+
+Recipe (all in FP64 NumPy, PCG64 streams, cast to complex64 at the end):
+  * per mixture a ``numpy.random.Generator(PCG64(seed))``;
+  * for k = 1, 2: a_k(f) ~ CN(0, I_M) for f = 0..F-1, R_k(f) = a_k a_k^H + delta I;
+  * v_k(n, f) = exp(sigma g), g ~ N(0, 1), drawn as [F][N] for k = 1 then k = 2;
+  * z ~ CN(0, I_M) drawn as [2][F][N][M]; x_k = sqrt(v_k) chol(R_k) z_k; y = x1 + x2.
+CN(0, 1) means real and imaginary parts each N(0, 1/2) (the pi^-M density of Eq. (like)).
+
+Initial parameters: b_j(f) ~ CN(0, I_M) from PCG64(seed + 1000 + j),
+S_j^(0)(f) = b_j b_j^H + I and v_j^(0)(n, f) = max(|y(n,f)|^2, eps_f) / (2 tr S_j^(0)(f)),
+eps_f = 1e-12 mean_n |y(n,f)|^2.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+BASE_SEED = 1805_06572
+
+
+@dataclasses.dataclass(frozen=True)
+class MixtureConfig:
+    name: str
+    M: int
+    F: int
+    N: int
+    iters: int
+    delta: float
+    sigma: float
+    storage: str = "c64"   # "c64" or "f16"
+
+
+# The workloads: small (M=2), mid (M=4, the benchmark workload), precision (M=8, FP16 y).
+CONFIGS = {
+    "small": MixtureConfig("small", M=2, F=257, N=300, iters=20, delta=0.1, sigma=1.0),
+    "mid": MixtureConfig("mid", M=4, F=513, N=1000, iters=50, delta=0.05, sigma=1.5),
+    "precision": MixtureConfig("precision", M=8, F=1025, N=4000, iters=100, delta=0.05,
+                               sigma=1.5, storage="f16"),
+}
+CONFIG_INDEX = {"small": 0, "mid": 1, "precision": 2, "batch": 3, "serve": 4}
+
+
+def config_seed(config: str, mixture_index: int = 0) -> int:
+    return BASE_SEED + 7919 * CONFIG_INDEX[config] + mixture_index
+
+
+def _cn(rng: np.random.Generator, shape) -> np.ndarray:
+    """Circular complex normal CN(0, 1) samples: real, imaginary parts N(0, 1/2)."""
+    g = rng.standard_normal(tuple(shape) + (2,))
+    return (g[..., 0] + 1j * g[..., 1]) / np.sqrt(2.0)
+
+
+def make_mixture(M: int, F: int, N: int, delta: float, sigma: float, seed: int):
+    """Draw one mixture. Returns dict with y (complex64 [F][N][M]), the true R [2][F][M][M]
+    (complex128), the true v [2][F][N] (float64) and the source images x [2][F][N][M]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = np.stack([_cn(rng, (F, M)) for _ in range(2)])                  # [2][F][M]
+    R = np.einsum("kfi,kfj->kfij", a, a.conj()) + delta * np.eye(M)     # [2][F][M][M]
+    v = np.stack([np.exp(sigma * rng.standard_normal((F, N))) for _ in range(2)])
+    z = _cn(rng, (2, F, N, M))
+    C = np.linalg.cholesky(R)                                           # R = C C^H
+    x = np.sqrt(v)[..., None] * np.einsum("kfij,kfnj->kfni", C, z)
+    y = (x[0] + x[1]).astype(np.complex64)
+    return {"y": y, "R": R, "v": v, "x": x.astype(np.complex64)}
+
+
+def init_params(y: np.ndarray, seed: int):
+    """Initial (v0 [2][F][N] float64, S0 [2][F][M][M] complex128) for mixture y [F][N][M]."""
+    F, N, M = y.shape
+    yd = y.astype(np.complex128)
+    S0 = np.empty((2, F, M, M), np.complex128)
+    for j in range(2):
+        rng = np.random.Generator(np.random.PCG64(seed + 1000 + j))
+        b = _cn(rng, (F, M))
+        S0[j] = np.einsum("fi,fj->fij", b, b.conj()) + np.eye(M)
+    pw = np.sum(np.abs(yd) ** 2, axis=2)                                # [F][N]
+    eps = 1e-12 * pw.mean(axis=1, keepdims=True)
+    tr = np.real(np.einsum("kfii->kf", S0))                             # [2][F]
+    v0 = np.maximum(pw, eps)[None] / (2.0 * tr[:, :, None])
+    return v0, S0
+
+
+def quantize_f16(y: np.ndarray):
+    """FP16 storage of y with a per-frequency power scale g_f = (mean_n |y|^2 / M)^(-1/2).
+
+    Returns (y16 float16 [F][N][M][2] interleaved re/im of g_f y, g float32 [F]) and the
+    dequantised complex128 mixture y16 / g_f that the EM actually sees."""
+    F, N, M = y.shape
+    yd = y.astype(np.complex128)
+    p = np.mean(np.abs(yd) ** 2, axis=(1, 2))
+    g = np.where(p > 0, 1.0 / np.sqrt(np.where(p > 0, p, 1.0)), 1.0).astype(np.float32)
+    s = yd * g.astype(np.float64)[:, None, None]
+    y16 = np.stack([s.real, s.imag], axis=-1).astype(np.float16)
+    deq = (y16[..., 0].astype(np.float64) + 1j * y16[..., 1].astype(np.float64)) \
+        / g.astype(np.float64)[:, None, None]
+    return y16, g, deq
+
+
+def make_config(name: str, mixture_index: int = 0, F: int | None = None):
+    """Mixture + initial params for a named workload (optionally with fewer bins)."""
+    c = CONFIGS[name]
+    seed = config_seed(name, mixture_index)
+    mix = make_mixture(c.M, F or c.F, c.N, c.delta, c.sigma, seed)
+    v0, S0 = init_params(mix["y"], seed)
+    return c, mix, v0, S0
