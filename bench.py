@@ -1,0 +1,360 @@
+"""Benchmark: TF-bin EM iterations per second of FastFCA (and conventional FCA) on GB300.
+
+One step = one whole EM job of the hot path on one mixture: load the mixture and initial
+parameters into the library state (device-resident inputs), the initial generalised
+eigendecomposition, L FastFCA iterations with the per-iteration log-likelihood, and the
+posterior-mean outputs (Algorithm 1). Workload: M=4 channels, F=513 bins, N=1000 frames,
+L=50 iterations, complex64, synthetic seeded mixture. bin-iters per step = F * N * L.
+
+Under torchrun each rank runs its own mixture (weak scaling: frequencies and mixtures are
+independent, there is no exchange on the data path); value = all ranks' bin-iters / the
+slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference of this project) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TF-bin EM iters/s, FastFCA vs frame-wise FCA on 1 GB300, rel err ≤1e-4 vs FP64"
+UNIT = "bin-iters/s"
+WORKLOAD = "mid"
+# FP32 peak derived from the unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes
+# x 2 flop per FMA x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def fast_flops_per_bin_iter(M: int) -> int:
+    """Algorithmic FP32 flops of one FastFCA time-frequency point per iteration (counted from
+    the equations: P^H y 8M^2; d, 1/d, |yt|^2, the mut coefficients 9M; the two v updates
+    9M+2; two rank-1-plus-diagonal Gram updates 2(5M^2+3M+1); log-likelihood terms 3M)."""
+    return 18 * M * M + 27 * M + 4
+
+
+def conv_flops_per_bin_iter(M: int) -> int:
+    """Algorithmic FP32 flops of one conventional time-frequency point per iteration: Rx
+    4M^2; Cholesky 4M^3/3; two triangular solves for u 8M^2; mu_1, mu_2 16M^2; L^-1 S_1 and
+    L^-1 S_2 8M^3; C = v1 v2 (L^-1 S1)^H (L^-1 S2), upper triangle 4M^3; two v updates 16M^2;
+    two Gram updates 2(5M^2+3M+1); log-likelihood terms 3M."""
+    return round(4 * M**3 / 3 + 8 * M**3 + 4 * M**3) + 4 * M * M + 8 * M * M + 16 * M * M \
+        + 16 * M * M + 2 * (5 * M * M + 3 * M + 1) + 3 * M
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("fca_fast.cu", "fca_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1805_06572_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("source_sha") != source_sha():
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, p in zip(names, parts[3:7]):
+                if p.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(mix, v0, S0, iters, n_bins, form="fast"):
+    """Time the FP64 oracle (as it stands) on a bounded sample: n_bins frequencies spread over
+    the band, all frames, all iterations. Returns (bin-iters/s, seconds, threads, sample)."""
+    import numpy as np
+
+    import oracle
+    F = mix["y"].shape[0]
+    fs = np.unique(np.linspace(0, F - 1, n_bins).round().astype(int))
+    y = mix["y"][fs].astype(np.complex128)
+    t0 = time.perf_counter()
+    oracle.em(form, y, v0[:, fs], S0[:, fs], iters, want_mu=True)
+    dt = time.perf_counter() - t0
+    units = len(fs) * y.shape[1] * iters
+    return units / dt, dt, oracle.threads(), f"{len(fs)} of {F} bins x N={y.shape[1]} x L={iters}"
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle timed on the host cores, one bounded sample per step."""
+    import synth
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    c, mix, v0, S0 = synth.make_config(WORKLOAD)
+    import oracle
+    oracle.build()
+    n_bins = c.F  # the whole workload per step: about a second on 16 cores
+    for _ in range(args.warmup):
+        cpu_oracle_rate(mix, v0, S0, c.iters, n_bins)
+    units, secs = 0.0, []
+    for _ in range(args.steps):
+        r, dt, threads, sample = cpu_oracle_rate(mix, v0, S0, c.iters, n_bins)
+        units += r * dt
+        secs.append(dt)
+    value = units / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"M={c.M} F={c.F} N={c.N} L={c.iters}, 2 sources, sampled bins",
+                   "form": "FastFCA (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1805_06572_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build()
+    from paper_1805_06572_gb300 import fca
+
+    dev = torch.device("cuda", local)
+    c, mix, v0, S0 = synth.make_config(WORKLOAD, mixture_index=rank)
+    F, N, M, L = c.F, c.N, c.M, c.iters
+    units = F * N * L
+    y_h = torch.from_numpy(mix["y"]).pin_memory()
+    v0_h = torch.from_numpy(v0).pin_memory()
+    S0_h = torch.from_numpy(S0).pin_memory()
+    y_d, v0_d, S0_d = y_h.to(dev), v0_h.to(dev), S0_h.to(dev)
+    st = fca.fca_init(y_d, v0_d, S0_d)
+    x1 = torch.empty((F, N, M), dtype=torch.complex64, device=dev)
+    x2 = torch.empty_like(x1)
+    ll = torch.empty(L, dtype=torch.float64, device=dev)
+    x1_h = torch.empty((F, N, M), dtype=torch.complex64).pin_memory()
+    x2_h = torch.empty_like(x1_h).pin_memory()
+    ll_h = torch.empty(L, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(form):
+        fca.fca_load(st, y_d, v0_d, S0_d)
+        (fca.fca_em_fast if form == "fast" else fca.fca_em_conventional)(st, L, ll)
+        fca.fca_separate(st, x1, x2, fca.FCA_SEP_ALG1)
+
+    def step_e2e():
+        fca.fca_load(st, y_h, v0_h, S0_h)
+        fca.fca_em_fast(st, L, ll)
+        fca.fca_separate(st, x1, x2, fca.FCA_SEP_ALG1)
+        x1_h.copy_(x1, non_blocking=True)
+        x2_h.copy_(x2, non_blocking=True)
+        ll_h.copy_(ll, non_blocking=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, form=None):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        kms = []
+        barrier()
+        launches0 = fca.fca_kernel_launches()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record()
+            fn() if form is None else fn(form)
+            evs[k][1].record()
+            if form is not None:
+                kms.append(fca.fca_last_em_kernel_ms(st))
+        barrier()
+        wall = time.perf_counter() - t0
+        launches = fca.fca_kernel_launches() - launches0
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, kms, wall, launches
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step("fast")
+    torch.cuda.synchronize()
+    code = fca.fca_sync_status(st)
+    if code != 0:
+        raise RuntimeError(f"device status {code} during warm-up")
+
+    with ClockSampler(local) as clk:
+        ms_fast, k_fast, wall_fast, launches = timed(step, args.steps, "fast")
+    clocks = clk.summary()
+    if fca.fca_sync_status(st) != 0:
+        raise RuntimeError("device status error in the timed region")
+
+    steps_conv = max(3, args.steps // 2)
+    for _ in range(3):
+        step("conventional")
+    ms_conv, k_conv, _, _ = timed(step, steps_conv, "conventional")
+    for _ in range(3):
+        step_e2e()
+    ms_e2e, _, _, _ = timed(step_e2e, args.steps)
+    if fca.fca_sync_status(st) != 0:
+        raise RuntimeError("device status error")
+
+    t_fast = max_over_ranks(sum(ms_fast) / 1e3)
+    t_conv = max_over_ranks(sum(ms_conv) / 1e3)
+    t_e2e = max_over_ranks(sum(ms_e2e) / 1e3)
+    value = world * units * args.steps / t_fast
+    conv_value = world * units * steps_conv / t_conv
+    e2e_value = world * units * args.steps / t_e2e
+    kern_fast = statistics.mean(k_fast) / 1e3
+    kern_conv = statistics.mean(k_conv) / 1e3
+    ach = fast_flops_per_bin_iter(M) * units / kern_fast / 1e12
+    ach_c = conv_flops_per_bin_iter(M) * units / kern_conv / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_over_ranks(statistics.mean(ms_fast)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"M={M} F={F} N={N} L={L}, 2 sources, complex64, seeded mixture "
+                               f"per rank (delta={c.delta}, sigma={c.sigma})",
+                   "form": "FastFCA", "l2": "flushed between steps (256 MiB write, outside the "
+                   "step events)", "parallelism": f"replicas x{world}",
+                   "step": "load + initial GEVD + L iterations with log-likelihood + "
+                           "posterior means"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP32_PEAK_TFLOPS,
+                     "traffic": profiled_traffic("fast_em_kernel_mid.md"),
+                     "kernel": "fast_em_kernel<4,c64,256>", "kernel_ms": 1e3 * kern_fast,
+                     "flops_per_bin_iter": fast_flops_per_bin_iter(M),
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "conventional": {"value": conv_value, "unit": UNIT, "ms_per_step": statistics.mean(ms_conv),
+                         "steps": steps_conv, "kernel_ms": 1e3 * kern_conv,
+                         "fast_speedup": value / conv_value,
+                         "roofline": {"bound": "alu", "achieved": ach_c, "peak": FP32_PEAK_TFLOPS,
+                                      "unit": "TFLOP/s", "frac": ach_c / FP32_PEAK_TFLOPS,
+                                      "flops_per_bin_iter": conv_flops_per_bin_iter(M)}},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": y_h.numel() * 8 + v0_h.numel() * 8 + S0_h.numel() * 16,
+                "d2h_bytes_per_step": x1_h.numel() * 8 * 2 + ll_h.numel() * 8,
+                "ms_per_step": statistics.mean(ms_e2e)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s_timed_region": wall_fast,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, threads, sample = cpu_oracle_rate(mix, v0, S0, L, F)
+        rate_c, dt_c, _, sample_c = cpu_oracle_rate(mix, v0, S0, L, 64, form="conventional")
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"FastFCA form, {sample} ({dt:.1f} s)",
+                                "conventional_value": rate_c,
+                                "conventional_sample": f"{sample_c} ({dt_c:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fca.fca_free(st)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,13 @@ fca_status fca_separate(fca_state* s, void* x1_dev, void* x2_dev, int32_t mode, 
  * on the device from (P, Lambda) in the FastFCA form, Eqs. (Sdiag), (recoverS)). */
 fca_status fca_get_params(fca_state* s, float* v_dev, double* S_host, void* cuda_stream);
 
+/* Per-frequency log-likelihood of the last EM call: out receives double [L][F] (L = that
+ * call's iteration count), entry (l, f) being the Eq. (like) term of bin f summed over the N
+ * frames at the parameters of iteration l. out may be device or host memory; a host
+ * destination synchronises the stream. Returns FCA_ERR_STATE if no EM call ran since the
+ * last load. *iters_out (may be NULL) receives L; with out == NULL the call only reports L. */
+fca_status fca_loglik_bins(fca_state* s, double* out, int32_t* iters_out, void* cuda_stream);
+
 /* Synchronise the stream and return the first device-side error of this state (FCA_OK if
  * none). */
 fca_status fca_sync_status(fca_state* s, void* cuda_stream);
@@ -124,6 +131,15 @@ fca_status fca_sync_status(fca_state* s, void* cuda_stream);
 /* Release the state and all its device memory. Synchronises the device first. NULL is a
  * no-op. */
 void fca_free(fca_state* s);
+
+/* Device duration (milliseconds) of the fused EM kernel launched by the last
+ * fca_em_fast / fca_em_conventional call, from CUDA events recorded on that call's stream
+ * just before and after the launch. Waits for the kernel to finish. FCA_ERR_STATE if no EM
+ * call ran since the last load. */
+fca_status fca_last_em_kernel_ms(fca_state* s, float* ms);
+
+/* Number of CUDA kernels this library has launched in this process (all states). */
+uint64_t fca_kernel_launches(void);
 
 /* Static description of a status code. */
 const char* fca_status_string(fca_status st);

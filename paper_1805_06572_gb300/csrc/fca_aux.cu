@@ -1,0 +1,248 @@
+// Per-frequency parameter kernels and small helpers (sm_103a).
+//
+//   gevd_from_S : (S1, S2) -> (P, Lambda, log det S2), the generalised eigenproblem of
+//                 Eq. (GEVD) (Algorithm 1, step 1, and the switch from the conventional
+//                 parameters to the FastFCA ones);
+//   S_from_P    : S2 = P^-H P^-1, S1 = P^-H Lambda P^-1 (Eqs. (Sdiag), (recoverS));
+//   sep_prep    : FP32 P^H, P^-H and Lambda for the posterior-mean kernel;
+//   prepare     : positivity floor of v per frequency, initial v (clamped);
+//   ll_reduce   : per-iteration log-likelihood summed over frequencies in a fixed order.
+// One warp handles one frequency bin; P^-1 is formed by Gauss-Jordan elimination with
+// partial pivoting in FP64 (these kernels run once per call, not once per iteration).
+#include "fca_dev.cuh"
+#include "fca_internal.h"
+
+namespace fca {
+
+constexpr int kWarpsPerCta = 4;
+
+// In-place inverse of the M x M matrix in aug[.][0..M) (aug[.][M..2M) must hold I); the
+// inverse ends in aug[.][M..2M). Returns false (uniformly) if a pivot is zero.
+template <int M>
+__device__ bool warp_inverse64(double2 (*aug)[2 * kMaxM], int lane) {
+  constexpr int W = 2 * M;
+  constexpr int kPer = (M * W + 31) / 32;
+  for (int k = 0; k < M; ++k) {
+    double mag = (lane >= k && lane < M) ? aug[lane][k].x * aug[lane][k].x + aug[lane][k].y * aug[lane][k].y : -1.0;
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, mag, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (om > mag || (om == mag && oi < idx)) {
+        mag = om;
+        idx = oi;
+      }
+    }
+    if (!(mag > 0.0) || !isfinite(mag)) return false;
+    const int piv = idx;
+    __syncwarp();
+    if (piv != k) {
+      for (int j = lane; j < W; j += 32) {
+        const double2 t = aug[k][j];
+        aug[k][j] = aug[piv][j];
+        aug[piv][j] = t;
+      }
+    }
+    __syncwarp();
+    const double2 p = aug[k][k];
+    const double dd = p.x * p.x + p.y * p.y;
+    const double2 inv = make_double2(p.x / dd, -p.y / dd);
+    __syncwarp();
+    for (int j = lane; j < W; j += 32) aug[k][j] = zmul(aug[k][j], inv);
+    __syncwarp();
+    double2 nv[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int e = lane + 32 * t;
+      if (e < M * W) {
+        const int i = e / W, j = e % W;
+        const double2 fac = aug[i][k];
+        nv[t] = (i == k) ? aug[i][j] : zadd(aug[i][j], zmul(make_double2(-fac.x, -fac.y), aug[k][j]));
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int e = lane + 32 * t;
+      if (e < M * W) aug[e / W][e % W] = nv[t];
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+template <int M>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) gevd_from_S_kernel(const ParamArgs a) {
+  __shared__ WarpLA la[kWarpsPerCta];
+  __shared__ float sig[kWarpsPerCta][kMaxM];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kWarpsPerCta + w;
+  if (f >= a.F) return;  // whole warp leaves together
+  const size_t MM = (size_t)M * M;
+  for (int e = lane; e < M * M; e += 32) {
+    la[w].A[e / M][e % M] = z2c(a.S[(size_t)f * MM + e]);
+    la[w].L[e / M][e % M] = z2c(a.S[((size_t)a.F + f) * MM + e]);
+  }
+  __syncwarp();
+  double ld = 0.0;
+  const int rc = warp_gevd<M>(la[w], lane, sig[w], &ld);
+  if (rc != kOk) {
+    if (lane == 0) set_status(a.status, rc);
+    return;
+  }
+  for (int e = lane; e < M * M; e += 32) a.P[(size_t)f * MM + e] = c2z(la[w].V[e / M][e % M]);
+  if (lane < M) a.lam[(size_t)f * M + lane] = (double)sig[w][lane];
+  if (lane == 0) a.logdetS2[f] = -ld;  // P = Q: log det S2 = -log|det P|^2
+}
+
+// mode 0: S_out = (P^-H Lam P^-1, P^-H P^-1); mode 1: separation prep.
+template <int M, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) from_P_kernel(const ParamArgs a) {
+  __shared__ double2 aug[kWarpsPerCta][kMaxM][2 * kMaxM];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kWarpsPerCta + w;
+  if (f >= a.F) return;
+  const size_t MM = (size_t)M * M;
+  double2(*A)[2 * kMaxM] = aug[w];
+  for (int e = lane; e < M * 2 * M; e += 32) {
+    const int i = e / (2 * M), j = e % (2 * M);
+    A[i][j] = (j < M) ? a.P[(size_t)f * MM + i * M + j] : make_double2(j - M == i ? 1.0 : 0.0, 0.0);
+  }
+  __syncwarp();
+  if (!warp_inverse64<M>(A, lane)) {
+    if (lane == 0) set_status(a.status, kErrNonFinite);
+    return;
+  }
+  // Pinv = A[.][M..2M)
+  if (MODE == 0) {
+    for (int e = lane; e < 2 * M * M; e += 32) {
+      const int j = e / (M * M), r = e % (M * M), i = r / M, k = r % M;
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {  // (P^-H T_j P^-1)_ik = sum_m conj(Pinv_mi) t_m Pinv_mk
+        const double2 pmi = zconj(A[m][M + i]);
+        const double t = (j == 0) ? a.lam[(size_t)f * M + m] : 1.0;
+        const double2 pmk = A[m][M + k];
+        s = zfma(make_double2(pmi.x * t, pmi.y * t), pmk, s);
+      }
+      a.S_out[((size_t)j * a.F + f) * MM + r] = s;
+    }
+  } else {
+    const float gi = a.ginv ? a.ginv[f] : 1.f;
+    for (int e = lane; e < M * M; e += 32) {
+      const int i = e / M, m = e % M;
+      const double2 p = a.P[(size_t)f * MM + m * M + i];  // (P^H)_im = conj(P_mi)
+      a.PH[(size_t)f * MM + e] = make_float2((float)p.x * gi, -(float)p.y * gi);
+      const double2 q = A[m][M + i];                      // (P^-H)_im = conj(Pinv_mi)
+      a.PinvH[(size_t)f * MM + e] = make_float2((float)q.x, -(float)q.y);
+    }
+    if (lane < M) a.lam32[(size_t)f * M + lane] = (float)a.lam[(size_t)f * M + lane];
+  }
+}
+
+template <int M, int ST>
+__global__ void __launch_bounds__(256) prepare_kernel(int F, int N, const void* y, const float* ginv,
+                                                      const double* v0, float* v, float* vfloor,
+                                                      int* status) {
+  using E = typename Elem<ST>::T;
+  __shared__ double part[8];
+  __shared__ float vf_s;
+  const int f = blockIdx.x, tid = threadIdx.x;
+  const E* yf = reinterpret_cast<const E*>(y) + (size_t)f * N * M;
+  float s = 0.f;
+  for (int i = tid; i < N * M; i += 256) s += cabs2(decode(yf[i]));
+  s = warp_sum(s);
+  if ((tid & 31) == 0) part[tid >> 5] = (double)s;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    const double g = (ST == 1) ? (double)ginv[f] : 1.0;
+    t *= g * g;
+    const double fl = fmax(1e-12 * t / ((double)N * M), 1e-30);
+    vf_s = (float)fl;
+    vfloor[f] = (float)fl;
+  }
+  __syncthreads();
+  const float vf = vf_s;
+  int bad = 0;
+  for (int j = 0; j < 2; ++j)
+    for (int n = tid; n < N; n += 256) {
+      const size_t i = ((size_t)j * F + f) * N + n;
+      const double x = v0[i];
+      bad |= !isfinite(x);
+      v[i] = fmaxf((float)x, vf);
+    }
+  if (__syncthreads_or(bad) && tid == 0) set_status(status, kErrNonFinite);
+}
+
+__global__ void ll_reduce_kernel(int F, const double* llf, double* ll) {
+  __shared__ double part[256];
+  const int l = blockIdx.x, tid = threadIdx.x;
+  double s = 0.0;
+  for (int f = tid; f < F; f += 256) s += llf[(size_t)l * F + f];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 128; o >= 1; o >>= 1) {
+    if (tid < o) part[tid] += part[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) ll[l] = part[0];
+}
+
+__global__ void invert_scale_kernel(int F, const float* g, float* ginv) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < F) ginv[f] = 1.0f / g[f];
+}
+
+// ------------------------------------------------------------------ host-side launchers
+#define FCA_DISPATCH_M(M, CALL)          \
+  switch (M) {                           \
+    case 1: { constexpr int kM = 1; CALL; } \
+    case 2: { constexpr int kM = 2; CALL; } \
+    case 3: { constexpr int kM = 3; CALL; } \
+    case 4: { constexpr int kM = 4; CALL; } \
+    case 5: { constexpr int kM = 5; CALL; } \
+    case 6: { constexpr int kM = 6; CALL; } \
+    case 7: { constexpr int kM = 7; CALL; } \
+    case 8: { constexpr int kM = 8; CALL; } \
+  }                                      \
+  return cudaErrorInvalidValue;
+
+cudaError_t launch_gevd_from_S(int M, const ParamArgs& a, cudaStream_t st) {
+  const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
+  FCA_DISPATCH_M(M, (gevd_from_S_kernel<kM><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
+}
+
+cudaError_t launch_S_from_P(int M, const ParamArgs& a, cudaStream_t st) {
+  const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
+  FCA_DISPATCH_M(M, (from_P_kernel<kM, 0><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
+}
+
+cudaError_t launch_sep_prep(int M, const ParamArgs& a, cudaStream_t st) {
+  const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
+  FCA_DISPATCH_M(M, (from_P_kernel<kM, 1><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
+}
+
+cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
+                           const double* v0, float* v, float* vfloor, int* status, cudaStream_t st) {
+  if (storage) {
+    FCA_DISPATCH_M(M, (prepare_kernel<kM, 1><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status)); return cudaGetLastError())
+  } else {
+    FCA_DISPATCH_M(M, (prepare_kernel<kM, 0><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status)); return cudaGetLastError())
+  }
+}
+
+cudaError_t launch_ll_reduce(int F, int iters, const double* llf, double* ll, cudaStream_t st) {
+  if (iters <= 0) return cudaSuccess;
+  ll_reduce_kernel<<<iters, 256, 0, st>>>(F, llf, ll);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_invert_scale(int F, const float* g, float* ginv, cudaStream_t st) {
+  invert_scale_kernel<<<(F + 255) / 256, 256, 0, st>>>(F, g, ginv);
+  return cudaGetLastError();
+}
+
+}  // namespace fca

@@ -1,0 +1,457 @@
+// Conventional FCA EM (Ito, Araki, Nakatani, arXiv 1805.06572, Sec. 2) on sm_103a.
+//
+// The plain form: every time-frequency point does the frame-wise matrix work the paper
+// names as the cost of FCA (Sec. 2, last paragraph). One CTA owns one frequency bin for
+// all iterations; one thread owns one time-frequency point at a time (FP32):
+//   Rx = v1 S1 + v2 S2, Cholesky Rx = L L^H
+//   u = Rx^-1 y, mu_j = v_j S_j u                                  Eq. (MMSE)
+//   C = v1 v2 S1 Rx^-1 S2 = v1 v2 (L^-1 S1)^H (L^-1 S2)            Eq. (postquadexp)
+//   Phi_j = mu_j mu_j^H + C
+//   v_j' = tr(S_j^-1 Phi_j) / M  (old S_j)                         Eq. (vupdate)
+//   Gram_j += Phi_j / v_j'                                          Eq. (Supdate)
+//   log-likelihood term -log det Rx - y^H Rx^-1 y                   Eq. (like)
+// then the CTA merges the Gram partial sums (FP32 warp transpose-reduction, FP64 across
+// warps) and sets S_j' = Gram_j / N in FP64. S_j^-1 for the next v update is formed once per
+// frequency per iteration by warp 0 (FP32 Cholesky of the FP64 S_j).
+#include "fca_dev.cuh"
+#include "fca_internal.h"
+
+namespace fca {
+
+template <int M, int NW>
+struct ConvShared {
+  static constexpr int V = 2 * M * M + 2;
+  static constexpr int VP = (V + 31) / 32 * 32;
+  float red[NW][VP];
+  double tot[VP];
+  double2 S[2][kMaxM][kMaxM];
+  float2 S32[2][M][M];
+  float2 Si32[2][M][M];
+  int fail;
+  WarpLA la;
+};
+
+__host__ __device__ constexpr int cpair_index(int M, int i, int k) {  // i < k
+  return i * (M - 1) - i * (i - 1) / 2 + (k - i - 1);
+}
+
+// FP32 inverse of the Hermitian positive definite FP64 matrix S (warp 0): S = L L^H,
+// S^-1 = L^-H L^-1. Returns false if S is not positive definite.
+template <int M>
+__device__ bool warp_hpd_inverse(WarpLA& la, const double2 (*S)[kMaxM], float2 (*S32)[M],
+                                 float2 (*Si)[M], int lane) {
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e % M;
+    const float2 s = z2c(S[i][j]);
+    la.L[i][j] = s;
+    S32[i][j] = s;
+  }
+  __syncwarp();
+  if (!warp_cholesky<M>(la, lane)) return false;
+  if (lane < M) {  // Z = L^-1 (column `lane` of the identity)
+    const int c = lane;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float2 s = make_float2(i == c ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < i; ++m) s = csub(s, cmul(la.L[i][m], la.Z[m][c]));
+      la.Z[i][c] = cscale(s, la.invd[i]);
+    }
+  }
+  __syncwarp();
+  for (int e = lane; e < M * M; e += 32) {  // Si = Z^H Z
+    const int i = e / M, j = e % M;
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < M; ++m) s = cadd(s, ccmul(la.Z[m][i], la.Z[m][j]));
+    Si[i][j] = s;
+  }
+  __syncwarp();
+  return true;
+}
+
+template <int M, int ST, int NT>
+__global__ void __launch_bounds__(NT) conv_em_kernel(const ConvEmArgs a) {
+  using E = typename Elem<ST>::T;
+  constexpr int NW = NT / 32;
+  using Sh = ConvShared<M, NW>;
+  constexpr int V = Sh::V, VP = Sh::VP, KP = VP / 32;
+  constexpr int MM = M * M;
+  __shared__ Sh sh;
+  extern __shared__ __align__(16) unsigned char dyn[];
+
+  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = a.N, F = a.F;
+  const size_t fN = (size_t)f * N;
+  const E* yg = reinterpret_cast<const E*>(a.y) + fN * M;
+  float* vg1 = a.v + fN;
+  float* vg2 = a.v + (size_t)F * N + fN;
+  E* ys = reinterpret_cast<E*>(dyn);
+  const size_t ybytes = ((size_t)N * M * sizeof(E) + 15) & ~(size_t)15;
+  float* vs = reinterpret_cast<float*>(dyn + ybytes);
+  const bool res = a.resident != 0;
+  const E* ysrc = res ? ys : yg;
+  float* v1p = res ? vs : vg1;
+  float* v2p = res ? vs + N : vg2;
+  const float vf = a.vfloor[f];
+  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+
+  for (int e = tid; e < 2 * MM; e += NT) {
+    const int j = e / MM, r = e % MM;
+    sh.S[j][r / M][r % M] = a.S[((size_t)j * F + f) * MM + r];
+  }
+  if (tid == 0) sh.fail = 0;
+  if (res) {
+    const size_t bytes = (size_t)N * M * sizeof(E);
+    if ((bytes & 15) == 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(yg);
+      uint4* dst = reinterpret_cast<uint4*>(ys);
+      for (size_t i = tid; i < bytes / 16; i += NT) dst[i] = src[i];
+    } else {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(yg);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(ys);
+      for (size_t i = tid; i < bytes / 4; i += NT) dst[i] = src[i];
+    }
+    for (int n = tid; n < N; n += NT) {
+      vs[n] = vg1[n];
+      vs[N + n] = vg2[n];
+    }
+  }
+  __syncthreads();
+
+  for (int it = 0; it < a.iters; ++it) {
+    const bool last = (it == a.iters - 1);
+    if (last) {
+      for (int e = tid; e < 2 * MM; e += NT) {
+        const int j = e / MM, r = e % MM;
+        a.S_prev[((size_t)j * F + f) * MM + r] = sh.S[j][r / M][r % M];
+      }
+    }
+    if (warp == 0) {
+      bool ok = warp_hpd_inverse<M>(sh.la, sh.S[0], sh.S32[0], sh.Si32[0], lane);
+      ok = ok && warp_hpd_inverse<M>(sh.la, sh.S[1], sh.S32[1], sh.Si32[1], lane);
+      if (!ok && lane == 0) {
+        set_status(a.status, kErrNotPD);
+        sh.fail = kErrNotPD;
+      }
+    }
+    __syncthreads();
+    if (sh.fail) break;
+
+    float acc[VP];
+#pragma unroll
+    for (int j = 0; j < VP; ++j) acc[j] = 0.f;
+    int bad = 0;
+    for (int n = tid; n < N; n += NT) {
+      float2 yv[M];
+      load_bin<M, ST>(ysrc + (size_t)n * M, yv);
+#pragma unroll
+      for (int i = 0; i < M; ++i) yv[i] = cscale(yv[i], gi);
+      const float v1 = v1p[n], v2 = v2p[n];
+      if (last) {
+        a.v_prev[fN + n] = v1;
+        a.v_prev[(size_t)F * N + fN + n] = v2;
+      }
+      // Cholesky of Rx = v1 S1 + v2 S2 (lower triangle), in registers.
+      float2 L[M][M];
+      LogProd lp;  // product of the Cholesky pivots = det Rx
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+#pragma unroll
+        for (int i = j; i < M; ++i) {
+          float2 s = cadd(cscale(sh.S32[0][i][j], v1), cscale(sh.S32[1][i][j], v2));
+#pragma unroll
+          for (int k = 0; k < j; ++k) s = csub(s, cmulc(L[i][k], L[j][k]));
+          if (i == j) {
+            const float piv = s.x;
+            bad |= !(piv > 0.f);
+            lp.mul(piv);
+            L[j][j] = make_float2(sqrtf(piv), rsqrtf(piv));  // (L_jj, 1/L_jj)
+          } else {
+            L[i][j] = cscale(s, L[j][j].y);
+          }
+        }
+      }
+      // w = L^-1 y, u = L^-H w = Rx^-1 y.
+      float2 w[M], u[M];
+      float quad = 0.f;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        float2 s = yv[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s = csub(s, cmul(L[i][k], w[k]));
+        w[i] = cscale(s, L[i][i].y);
+        quad += cabs2(w[i]);
+      }
+#pragma unroll
+      for (int i = M - 1; i >= 0; --i) {
+        float2 s = w[i];
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) s = csub(s, ccmul(L[k][i], u[k]));
+        u[i] = cscale(s, L[i][i].y);
+      }
+      // mu_j = v_j S_j u.
+      float2 mu1[M], mu2[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          s1 = cfma(sh.S32[0][i][k], u[k], s1);
+          s2 = cfma(sh.S32[1][i][k], u[k], s2);
+        }
+        mu1[i] = cscale(s1, v1);
+        mu2[i] = cscale(s2, v2);
+      }
+      // A = L^-1 S1, B = L^-1 S2 (column by column), C = v1 v2 A^H B (upper triangle).
+      float2 A[M][M], B[M][M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          float2 sa = sh.S32[0][i][c], sb = sh.S32[1][i][c];
+#pragma unroll
+          for (int k = 0; k < i; ++k) {
+            sa = csub(sa, cmul(L[i][k], A[k][c]));
+            sb = csub(sb, cmul(L[i][k], B[k][c]));
+          }
+          A[i][c] = cscale(sa, L[i][i].y);
+          B[i][c] = cscale(sb, L[i][i].y);
+        }
+      }
+      const float v12 = v1 * v2;
+      float2 C[M][M];
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = i; k < M; ++k) {
+          float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int m = 0; m < M; ++m) s = cadd(s, ccmul(A[m][i], B[m][k]));
+          C[i][k] = cscale(s, v12);
+          if (k == i) C[i][i].y = 0.f;
+        }
+      // v_j' = (mu_j^H S_j^-1 mu_j + tr(S_j^-1 C)) / M with the old S_j (Eq. (vupdate)).
+      float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        t1 += sh.Si32[0][i][i].x * (cabs2(mu1[i]) + C[i][i].x);
+        t2 += sh.Si32[1][i][i].x * (cabs2(mu2[i]) + C[i][i].x);
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) {
+          // 2 Re(conj(mu_i) Si_ik mu_k) + 2 Re(Si_ik conj(C_ik))
+          const float2 z1 = cmul(sh.Si32[0][i][k], mu1[k]);
+          const float2 z2 = cmul(sh.Si32[1][i][k], mu2[k]);
+          t1 += 2.f * (fmaf(mu1[i].x, z1.x, mu1[i].y * z1.y) +
+                       fmaf(sh.Si32[0][i][k].x, C[i][k].x, sh.Si32[0][i][k].y * C[i][k].y));
+          t2 += 2.f * (fmaf(mu2[i].x, z2.x, mu2[i].y * z2.y) +
+                       fmaf(sh.Si32[1][i][k].x, C[i][k].x, sh.Si32[1][i][k].y * C[i][k].y));
+        }
+      }
+      const float v1n = fmaxf(t1 * (1.f / M), vf);
+      const float v2n = fmaxf(t2 * (1.f / M), vf);
+      v1p[n] = v1n;
+      v2p[n] = v2n;
+      const float w1 = __fdividef(1.f, v1n), w2 = __fdividef(1.f, v2n);
+      // Gram_j += (mu_j mu_j^H + C) / v_j' (upper triangle).
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        acc[i] += (cabs2(mu1[i]) + C[i][i].x) * w1;
+        acc[MM + i] += (cabs2(mu2[i]) + C[i][i].x) * w2;
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) {
+          const int o = M + 2 * cpair_index(M, i, k);
+          const float2 z1 = cadd(cmulc(mu1[i], mu1[k]), C[i][k]);
+          const float2 z2 = cadd(cmulc(mu2[i], mu2[k]), C[i][k]);
+          acc[o] = fmaf(z1.x, w1, acc[o]);
+          acc[o + 1] = fmaf(z1.y, w1, acc[o + 1]);
+          acc[MM + o] = fmaf(z2.x, w2, acc[MM + o]);
+          acc[MM + o + 1] = fmaf(z2.y, w2, acc[MM + o + 1]);
+        }
+      }
+      acc[2 * MM] += lp.log();
+      acc[2 * MM + 1] += quad;
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) {
+        set_status(a.status, kErrNotPD);
+        sh.fail = kErrNotPD;
+      }
+    }
+
+    warp_transpose_reduce<VP>(acc, lane);
+#pragma unroll
+    for (int j = 0; j < KP; ++j) sh.red[warp][KP * lane + j] = acc[j];
+    __syncthreads();
+    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s[w & 3] += (double)sh.red[w][i];
+      sh.tot[i] = (s[0] + s[1]) + (s[2] + s[3]);
+    }
+    __syncthreads();
+    const double invN = 1.0 / (double)N;
+    for (int e = tid; e < 2 * MM; e += NT) {  // S_j' = Gram_j / N (Eq. (Supdate))
+      const int j = e / MM, r = e % MM, i = r / M, k = r % M;
+      double2 s;
+      if (i == k) {
+        s = make_double2(sh.tot[j * MM + i] * invN, 0.0);
+      } else {
+        const int lo = min(i, k), hi = max(i, k);
+        const int o = j * MM + M + 2 * cpair_index(M, lo, hi);
+        s = make_double2(sh.tot[o] * invN, (i < k ? 1.0 : -1.0) * sh.tot[o + 1] * invN);
+      }
+      sh.S[j][i][k] = s;
+    }
+    if (tid == 0) {
+      const double ll = -(double)N * M * 1.1447298858494002 - sh.tot[2 * MM] - sh.tot[2 * MM + 1];
+      a.llf[(size_t)it * F + f] = ll;
+      if (!isfinite(ll)) {
+        set_status(a.status, kErrNonFinite);
+        sh.fail = kErrNonFinite;
+      }
+    }
+    __syncthreads();
+    if (sh.fail) break;
+  }
+
+  for (int e = tid; e < 2 * MM; e += NT) {
+    const int j = e / MM, r = e % MM;
+    a.S[((size_t)j * F + f) * MM + r] = sh.S[j][r / M][r % M];
+  }
+  if (res) {
+    for (int n = tid; n < N; n += NT) {
+      vg1[n] = vs[n];
+      vg2[n] = vs[N + n];
+    }
+  }
+}
+
+// Posterior means of the conventional form, mu_j = v_j S_j (v1 S1 + v2 S2)^-1 y (Eq. (MMSE)).
+template <int M, int ST>
+__global__ void __launch_bounds__(256) sep_conv_kernel(const SepConvArgs a) {
+  using E = typename Elem<ST>::T;
+  __shared__ float2 S32[2][M][M];
+  const int f = blockIdx.y, tid = threadIdx.x;
+  const size_t MM = (size_t)M * M;
+  if (tid < 2 * M * M) {
+    const int j = tid / (M * M), r = tid % (M * M);
+    S32[j][r / M][r % M] = z2c(a.S[((size_t)j * a.F + f) * MM + r]);
+  }
+  __syncthreads();
+  const int n = blockIdx.x * 256 + tid;
+  if (n >= a.N) return;
+  const size_t b = (size_t)f * a.N + n;
+  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+  float2 yv[M];
+  load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + b * M, yv);
+  const float v1 = a.v[b], v2 = a.v[(size_t)a.F * a.N + b];
+  float2 L[M][M];
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < M; ++j)
+#pragma unroll
+    for (int i = j; i < M; ++i) {
+      float2 s = cadd(cscale(S32[0][i][j], v1), cscale(S32[1][i][j], v2));
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = csub(s, cmulc(L[i][k], L[j][k]));
+      if (i == j) {
+        bad |= !(s.x > 0.f);
+        L[j][j] = make_float2(sqrtf(s.x), rsqrtf(s.x));
+      } else {
+        L[i][j] = cscale(s, L[j][j].y);
+      }
+    }
+  if (bad) set_status(a.status, kErrNotPD);
+  float2 w[M], u[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 s = cscale(yv[i], gi);
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = csub(s, cmul(L[i][k], w[k]));
+    w[i] = cscale(s, L[i][i].y);
+  }
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i) {
+    float2 s = w[i];
+#pragma unroll
+    for (int k = i + 1; k < M; ++k) s = csub(s, ccmul(L[k][i], u[k]));
+    u[i] = cscale(s, L[i][i].y);
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      s1 = cfma(S32[0][i][k], u[k], s1);
+      s2 = cfma(S32[1][i][k], u[k], s2);
+    }
+    a.x1[b * M + i] = cscale(s1, v1);
+    a.x2[b * M + i] = cscale(s2, v2);
+  }
+}
+
+// ------------------------------------------------------------------ host-side launchers
+template <int M, int ST, int NT>
+static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
+  size_t dyn = a.resident ? em_dyn_smem(M, ST, a.N) : 0;
+  auto k = conv_em_kernel<M, ST, NT>;
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<a.F, NT, dyn, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int M, int ST>
+static cudaError_t launch_conv_m(const ConvEmArgs& a, cudaStream_t st) {
+  return em_threads(M, a.N) == 128 ? launch_conv_t<M, ST, 128>(a, st) : launch_conv_t<M, ST, 256>(a, st);
+}
+
+template <int ST>
+static cudaError_t launch_conv_s(int M, const ConvEmArgs& a, cudaStream_t st) {
+  switch (M) {
+    case 1: return launch_conv_m<1, ST>(a, st);
+    case 2: return launch_conv_m<2, ST>(a, st);
+    case 3: return launch_conv_m<3, ST>(a, st);
+    case 4: return launch_conv_m<4, ST>(a, st);
+    case 5: return launch_conv_m<5, ST>(a, st);
+    case 6: return launch_conv_m<6, ST>(a, st);
+    case 7: return launch_conv_m<7, ST>(a, st);
+    case 8: return launch_conv_m<8, ST>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_conv_em(int M, int storage, const ConvEmArgs& a, cudaStream_t st) {
+  return storage ? launch_conv_s<1>(M, a, st) : launch_conv_s<0>(M, a, st);
+}
+
+template <int M, int ST>
+static cudaError_t launch_sep_conv_m(const SepConvArgs& a, cudaStream_t st) {
+  dim3 grid((a.N + 255) / 256, a.F);
+  sep_conv_kernel<M, ST><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_sep_conv_s(int M, const SepConvArgs& a, cudaStream_t st) {
+  switch (M) {
+    case 1: return launch_sep_conv_m<1, ST>(a, st);
+    case 2: return launch_sep_conv_m<2, ST>(a, st);
+    case 3: return launch_sep_conv_m<3, ST>(a, st);
+    case 4: return launch_sep_conv_m<4, ST>(a, st);
+    case 5: return launch_sep_conv_m<5, ST>(a, st);
+    case 6: return launch_sep_conv_m<6, ST>(a, st);
+    case 7: return launch_sep_conv_m<7, ST>(a, st);
+    case 8: return launch_sep_conv_m<8, ST>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sep_conv(int M, int storage, const SepConvArgs& a, cudaStream_t st) {
+  return storage ? launch_sep_conv_s<1>(M, a, st) : launch_sep_conv_s<0>(M, a, st);
+}
+
+}  // namespace fca

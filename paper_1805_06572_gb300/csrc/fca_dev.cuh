@@ -1,0 +1,413 @@
+// Device building blocks shared by the FCA kernels (sm_103a).
+//
+//   * complex64 / complex128 arithmetic on float2 / double2;
+//   * a warp "transpose" reduction: V per-lane partial sums -> each lane ends with V/32
+//     complete warp sums (31 shuffles for 32 values instead of 160 for a butterfly each);
+//   * dense Hermitian linear algebra for one frequency bin inside one warp (M <= 8):
+//     Cholesky, triangular solves, cyclic Jacobi with the round-robin (parallel) ordering,
+//     used for the generalised eigenproblem of Eq. (GEVD) on the FP32 pipe, plus FP64
+//     matrix products for the basis update P <- P Q (Eq. (updatePeff)).
+//
+// Why the eigensolver runs on the FP32 pipe: on GB300 an FP64 FMA has ~64 cycles of
+// latency, FP64 division and square root ~650 cycles, and FP64 throughput is 1/62 of FP32
+// (measured). A Jacobi sweep is a chain of dependent rotations, so an FP64 solver would
+// cost more than the whole per-bin pass of an EM iteration. FP64 is kept where the sums are
+// long or the product chain is long: the cross-warp merge of the Gram and log-likelihood
+// partial sums, and the accumulated basis P.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fca {
+
+constexpr int kMaxM = 8;
+
+// Device status codes (mirror fca_status in fca.h).
+enum : int { kOk = 0, kErrNotPD = 4, kErrEigNoConv = 5, kErrNonFinite = 6 };
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------------- complex64
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 ccmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+// a * b + c
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// ------------------------------------------------------------------------ complex128
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ float2 z2c(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 c2z(float2 a) { return make_double2((double)a.x, (double)a.y); }
+
+// ------------------------------------------------------------------ storage decoding
+template <int ST> struct Elem;
+template <> struct Elem<0> { typedef float2 T; };   // complex64
+template <> struct Elem<1> { typedef __half2 T; };  // FP16 pair
+
+__device__ __forceinline__ float2 decode(float2 v) { return v; }
+__device__ __forceinline__ float2 decode(__half2 v) { return __half22float2(v); }
+
+// Load the M-vector of one time-frequency point. `p` points at its first element.
+template <int M, int ST>
+__device__ __forceinline__ void load_bin(const typename Elem<ST>::T* p, float2 (&y)[M]) {
+  if constexpr (ST == 0) {
+    if constexpr ((M & 1) == 0) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+      for (int i = 0; i < M / 2; ++i) {
+        float4 t = q[i];
+        y[2 * i] = make_float2(t.x, t.y);
+        y[2 * i + 1] = make_float2(t.z, t.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < M; ++i) y[i] = p[i];
+    }
+  } else {
+    if constexpr ((M & 3) == 0) {
+      const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+      for (int i = 0; i < M / 4; ++i) {
+        uint4 t = q[i];
+        const __half2* h = reinterpret_cast<const __half2*>(&t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) y[4 * i + k] = __half22float2(h[k]);
+      }
+    } else if constexpr ((M & 1) == 0) {
+      const uint2* q = reinterpret_cast<const uint2*>(p);
+#pragma unroll
+      for (int i = 0; i < M / 2; ++i) {
+        uint2 t = q[i];
+        const __half2* h = reinterpret_cast<const __half2*>(&t);
+        y[2 * i] = __half22float2(h[0]);
+        y[2 * i + 1] = __half22float2(h[1]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < M; ++i) y[i] = __half22float2(p[i]);
+    }
+  }
+}
+
+// ------------------------------------------------------------- accurate log of a product
+// log of a product of positive normal floats, accumulated as (mantissa product, exponent sum)
+// so that neither overflows: each factor contributes its mantissa in [1, 2) and its binary
+// exponent; one correctly-rounded-to-1-ulp logf at the end replaces one approximate log per
+// factor.
+struct LogProd {
+  float m = 1.f;
+  int e = 0;
+  __device__ __forceinline__ void mul(float x) {
+    const int b = __float_as_int(x);
+    e += (b >> 23) - 127;
+    m *= __int_as_float((b & 0x007fffff) | 0x3f800000);
+  }
+  // Call at most every 8 factors (m < 2^8) to keep m in range.
+  __device__ __forceinline__ float log() const { return logf(m) + 0.6931471805599453f * (float)e; }
+};
+
+// ------------------------------------------------------------ warp transpose reduction
+// acc[0..VP) holds this lane's partial sums (VP a multiple of 32). Afterwards lane l holds,
+// in acc[0..VP/32), the warp-wide sums of values [l*VP/32, (l+1)*VP/32).
+template <int VP>
+__device__ __forceinline__ void warp_transpose_reduce(float (&acc)[VP], int lane) {
+  static_assert(VP % 32 == 0, "VP must be a multiple of 32");
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int o = 16 >> r;
+    const int h = VP >> (r + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      float send = up ? acc[j] : acc[j + h];
+      float keep = up ? acc[j + h] : acc[j];
+      acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// --------------------------------------------------- warp-level dense Hermitian algebra
+// Matrices are row-major with leading dimension kMaxM, in shared memory. Every function is
+// called by all 32 lanes of one warp and ends with __syncwarp().
+struct WarpLA {
+  float2 A[kMaxM][kMaxM];   // work matrix (eigenproblem)
+  float2 L[kMaxM][kMaxM];   // Cholesky factor (lower triangle)
+  float2 Z[kMaxM][kMaxM];   // temporary
+  float2 V[kMaxM][kMaxM];   // eigenvectors / result
+  float invd[kMaxM];        // 1 / L_ii
+  float2 jself[kMaxM + 1];  // Jacobi: J_xx for every index x
+  float2 joth[kMaxM + 1];   // Jacobi: J_{partner(x), x}
+  int partner[kMaxM + 1];
+};
+
+// In-place Cholesky B = L L^H of the Hermitian positive definite matrix in la.L (the lower
+// triangle is read and overwritten). Returns false (uniformly across the warp) if a pivot is
+// not positive and finite.
+template <int M>
+__device__ bool warp_cholesky(WarpLA& la, int lane) {
+  for (int k = 0; k < M; ++k) {
+    __syncwarp();
+    const float bkk = la.L[k][k].x;
+    if (!(bkk > 0.f) || !(bkk < 3.0e38f)) {
+      __syncwarp();
+      return false;
+    }
+    const float lkk = sqrtf(bkk);
+    const float il = 1.0f / lkk;
+    __syncwarp();
+    if (lane == k) {
+      la.L[k][k] = make_float2(lkk, 0.f);
+      la.invd[k] = il;
+    } else if (lane > k && lane < M) {
+      la.L[lane][k] = cscale(la.L[lane][k], il);
+    }
+    __syncwarp();
+    for (int e = lane; e < M * M; e += 32) {
+      const int i = e / M, j = e - (e / M) * M;
+      if (j > k && i >= j) la.L[i][j] = csub(la.L[i][j], cmulc(la.L[i][k], la.L[j][k]));
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+// la.A <- L^-1 A L^-H for Hermitian A (in la.A), using la.L / la.invd; la.Z and la.V are
+// clobbered.
+template <int M>
+__device__ void warp_congruence_inv(WarpLA& la, int lane) {
+  if (lane < M) {  // Z = L^-1 A, column `lane`
+    const int c = lane;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float2 s = la.A[i][c];
+#pragma unroll
+      for (int m = 0; m < i; ++m) s = csub(s, cmul(la.L[i][m], la.Z[m][c]));
+      la.Z[i][c] = cscale(s, la.invd[i]);
+    }
+  }
+  __syncwarp();
+  if (lane < M) {  // V = L^-1 Z^H, column `lane` (Z^H = A L^-H since A is Hermitian)
+    const int c = lane;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float2 s = cconj(la.Z[c][i]);
+#pragma unroll
+      for (int m = 0; m < i; ++m) s = csub(s, cmul(la.L[i][m], la.V[m][c]));
+      la.V[i][c] = cscale(s, la.invd[i]);
+    }
+  }
+  __syncwarp();
+  // Hermitian part into A.
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e - (e / M) * M;
+    float2 a = la.V[i][j], b = la.V[j][i];
+    la.A[i][j] = (i == j) ? make_float2(a.x, 0.f) : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+  }
+  __syncwarp();
+}
+
+// Cyclic Jacobi eigendecomposition of the Hermitian matrix in la.A: on return la.A is
+// (numerically) diagonal with the eigenvalues on its diagonal and la.V holds the
+// eigenvectors (A_in = V diag V^H). Rotations use the round-robin ordering, so the M/2
+// rotations of one round are disjoint and applied together by all lanes. A pair is rotated
+// when |a_pq|^2 > tol^2 |a_pp a_qq|. Returns the number of sweeps, or -1 on the sweep cap.
+template <int M>
+__device__ int warp_jacobi(WarpLA& la, int lane, float tol, int max_sweeps) {
+  constexpr int n = M + (M & 1);  // even number of positions (a dummy index when M is odd)
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e - (e / M) * M;
+    la.V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncwarp();
+  if (M == 1) return 0;
+  const float tol2 = tol * tol;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < n - 1; ++r) {
+      if (lane < n / 2) {
+        const int k = lane;
+        const int a = (k == 0) ? r : (r + k) % (n - 1);
+        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
+        const int p = min(a, b), q = max(a, b);
+        float c = 1.f, s = 0.f;
+        float2 e = make_float2(1.f, 0.f);
+        if (q < M) {
+          const float app = la.A[p][p].x, aqq = la.A[q][q].x;
+          const float2 apq = la.A[p][q];
+          const float r2 = cabs2(apq);
+          if (r2 > tol2 * fabsf(app * aqq) && r2 > 1e-36f) {
+            const float rr = sqrtf(r2);
+            const float tau = (aqq - app) / (2.f * rr);
+            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+            c = 1.0f / sqrtf(fmaf(t, t, 1.f));  // correctly rounded: |det J| stays close to 1
+            s = t * c;
+            e = cscale(apq, 1.f / rr);
+            rotated = 1;
+          }
+          // J_pp = c, J_qp = -s conj(e), J_pq = s, J_qq = c conj(e)
+          la.jself[p] = make_float2(c, 0.f);
+          la.joth[p] = cscale(cconj(e), -s);
+          la.partner[p] = q;
+          la.jself[q] = cscale(cconj(e), c);
+          la.joth[q] = make_float2(s, 0.f);
+          la.partner[q] = p;
+        } else {
+          la.jself[p] = make_float2(1.f, 0.f);
+          la.joth[p] = make_float2(0.f, 0.f);
+          la.partner[p] = p;
+        }
+      }
+      __syncwarp();
+      // new A_il = conj(J_ii)(A_il J_ll + A_il' J_l'l) + conj(J_i'i)(A_i'l J_ll + A_i'l' J_l'l)
+      constexpr int kPer = (M * M + 31) / 32;
+      float2 na[kPer], nv[kPer];
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = lane + 32 * t;
+        if (e < M * M) {
+          const int i = e / M, l = e - (e / M) * M;
+          const int ip = la.partner[i], lp = la.partner[l];
+          const float2 Ji = la.jself[i], Jo_i = la.joth[i], Jl = la.jself[l], Jo_l = la.joth[l];
+          const float2 r0 = cfma(la.A[i][lp], Jo_l, cmul(la.A[i][l], Jl));
+          const float2 r1 = cfma(la.A[ip][lp], Jo_l, cmul(la.A[ip][l], Jl));
+          na[t] = cadd(ccmul(Ji, r0), ccmul(Jo_i, r1));
+          nv[t] = cfma(la.V[i][lp], Jo_l, cmul(la.V[i][l], Jl));
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = lane + 32 * t;
+        if (e < M * M) {
+          const int i = e / M, l = e - (e / M) * M;
+          float2 v = na[t];
+          if (i == l) v.y = 0.f;
+          else if (la.partner[i] == l) v = make_float2(0.f, 0.f);  // the pivot pair
+          la.A[i][l] = v;
+          la.V[i][l] = nv[t];
+        }
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, rotated)) return sweep + 1;
+  }
+  return -1;
+}
+
+// la.V <- L^-H la.V (back substitution, one column per lane).
+template <int M>
+__device__ void warp_backsolve_LH(WarpLA& la, int lane) {
+  if (lane < M) {
+    const int c = lane;
+    float2 q[M];
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+      float2 s = la.V[i][c];
+#pragma unroll
+      for (int m = i + 1; m < M; ++m) s = csub(s, ccmul(la.L[m][i], q[m]));
+      q[i] = cscale(s, la.invd[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) la.Z[i][c] = q[i];
+  }
+  __syncwarp();
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e - (e / M) * M;
+    la.V[i][j] = la.Z[i][j];
+  }
+  __syncwarp();
+}
+
+// Generalised eigenproblem of the Hermitian pencil (A, B), B positive definite, given in
+// la.A (A) and la.L (B): Cholesky B = L L^H, W = L^-1 A L^-H = U Sig U^H (Jacobi),
+// Q = L^-H U, so that Q^H B Q = I and Q^H A Q = Sig (Eq. (GEVDeff5)). On return la.V = Q and
+// sig[i] = Sig_ii. *logdetQ receives log|det Q|^2 of the Q actually returned:
+// -log det B + log|det U|^2, where the FP32 rotations leave U unitary only to rounding, so
+// log|det U|^2 = log det(U^H U) = ||U||_F^2 - M to first order in U^H U - I (FP64 sum).
+// Returns a device status code.
+template <int M>
+__device__ int warp_gevd(WarpLA& la, int lane, float* sig, double* logdetQ) {
+  if (!warp_cholesky<M>(la, lane)) return kErrNotPD;
+  float ld = (lane < M) ? 2.f * logf(la.L[lane][lane].x) : 0.f;
+  ld = warp_sum(ld);
+  warp_congruence_inv<M>(la, lane);
+  const int sw = warp_jacobi<M>(la, lane, 2.0e-7f, 30);
+  if (sw < 0) return kErrEigNoConv;
+  if (lane < M) sig[lane] = la.A[lane][lane].x;
+  double un = 0.0;
+  for (int e = lane; e < M * M; e += 32) {
+    const float2 u = la.V[e / M][e % M];
+    un = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, un));
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+  warp_backsolve_LH<M>(la, lane);
+  __syncwarp();
+  *logdetQ = (un - (double)M) - (double)ld;
+  for (int i = 0; i < M; ++i) {
+    const float s = sig[i];
+    if (!(s > 0.f) || !(s < 3.0e38f)) return kErrNotPD;
+  }
+  return kOk;
+}
+
+// P <- P Q in FP64 (Eq. (updatePeff)); P in shared memory [M][M] double2, Q = la.V (FP32).
+template <int M>
+__device__ void warp_update_basis(double2 (*P)[kMaxM], const WarpLA& la, int lane) {
+  constexpr int kPer = (M * M + 31) / 32;
+  double2 out[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = lane + 32 * t;
+    if (e < M * M) {
+      const int i = e / M, c = e - (e / M) * M;
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int m = 0; m < M; ++m) s = zfma(P[i][m], c2z(la.V[m][c]), s);
+      out[t] = s;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = lane + 32 * t;
+    if (e < M * M) {
+      const int i = e / M, c = e - (e / M) * M;
+      P[i][c] = out[t];
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace fca

@@ -1,0 +1,400 @@
+// FastFCA (Ito, Araki, Nakatani, arXiv 1805.06572, Sec. 3, Algorithm 1) on sm_103a.
+//
+// One CTA owns one frequency bin f for all L iterations (every quantity of the EM is
+// indexed by f and Eq. (like) factorises over f, so CTAs never communicate). Per iteration:
+//   bin pass (FP32, one thread per time-frequency point, frames strided over the CTA):
+//     yt = P^H y                                        Eq. (tildey)
+//     d_i = v1 lam_i + v2, mut1 = v1 lam yt / d,        Eq. (MMSEtilde)
+//       mut2 = v2 yt / d
+//     c_i = v1 v2 lam_i / d_i                           Eq. (updatePhitildeeff), diagonal
+//     v1' = (1/M) sum_i (|mut1_i|^2 + c_i) / lam_i      Eq. (updateveff)
+//     v2' = (1/M) sum_i (|mut2_i|^2 + c_i)
+//     St_j += (mut_j mut_j^H + diag(c)) / v_j'          Eq. (updateStildeeff), partial sums
+//     log-likelihood terms log d_i + |yt_i|^2 / d_i     Eq. (like) in the transformed basis
+//   CTA reduction: per-lane FP32 partials -> warp transpose-reduction (FP32) -> cross-warp
+//     merge in FP64, in a fixed order (bitwise reproducible);
+//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8), P <- P Q in FP64
+//     (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)),
+//     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use).
+// The log-likelihood of iteration l uses log det Rx = sum_i log d_i + log det S2 and
+// y^H Rx^-1 y = sum_i |yt_i|^2 / d_i, which follow from Rx = P^-H (v1 Lam + v2 I) P^-1.
+// The mixture and v stay in shared memory across iterations when they fit.
+#include "fca_dev.cuh"
+#include "fca_internal.h"
+
+namespace fca {
+
+template <int M, int NW>
+struct FastShared {
+  static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
+  static constexpr int VP = (V + 31) / 32 * 32;
+  float red[NW][VP];
+  double tot[VP];
+  double2 P[kMaxM][kMaxM];
+  float2 PH[M][M];   // FP32 P^H, times the decode scale
+  float lam[M], ilam[M];
+  double lam64[kMaxM];
+  float sig[kMaxM];
+  double logdetS2;
+  int fail;
+  WarpLA la;
+};
+
+__host__ __device__ constexpr int pair_index(int M, int i, int k) {  // i < k
+  return i * (M - 1) - i * (i - 1) / 2 + (k - i - 1);
+}
+
+template <int M, int ST, int NT>
+__global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
+  using E = typename Elem<ST>::T;
+  constexpr int NW = NT / 32;
+  using Sh = FastShared<M, NW>;
+  constexpr int V = Sh::V, VP = Sh::VP, KP = VP / 32;
+  constexpr int MM = M * M;
+  constexpr bool kHoist = (M <= 4);
+  __shared__ Sh sh;
+  extern __shared__ __align__(16) unsigned char dyn[];
+
+  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = a.N, F = a.F;
+  const size_t fN = (size_t)f * N;
+  const E* yg = reinterpret_cast<const E*>(a.y) + fN * M;
+  float* vg1 = a.v + fN;
+  float* vg2 = a.v + (size_t)F * N + fN;
+  E* ys = reinterpret_cast<E*>(dyn);
+  const size_t ybytes = ((size_t)N * M * sizeof(E) + 15) & ~(size_t)15;
+  float* vs = reinterpret_cast<float*>(dyn + ybytes);
+  const bool res = a.resident != 0;
+  const E* ysrc = res ? ys : yg;
+  float* v1p = res ? vs : vg1;
+  float* v2p = res ? vs + N : vg2;
+  const float vf = a.vfloor[f];
+  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+
+  if (tid < MM) sh.P[tid / M][tid % M] = a.P[(size_t)f * MM + tid];
+  if (tid < M) {
+    const double l = a.lam[(size_t)f * M + tid];
+    sh.lam64[tid] = l;
+    sh.lam[tid] = (float)l;
+    sh.ilam[tid] = 1.f / (float)l;
+  }
+  if (tid == 0) {
+    sh.logdetS2 = a.logdetS2[f];
+    sh.fail = 0;
+  }
+  if (res) {
+    const size_t bytes = (size_t)N * M * sizeof(E);
+    if ((bytes & 15) == 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(yg);
+      uint4* dst = reinterpret_cast<uint4*>(ys);
+      for (size_t i = tid; i < bytes / 16; i += NT) dst[i] = src[i];
+    } else {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(yg);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(ys);
+      for (size_t i = tid; i < bytes / 4; i += NT) dst[i] = src[i];
+    }
+    for (int n = tid; n < N; n += NT) {
+      vs[n] = vg1[n];
+      vs[N + n] = vg2[n];
+    }
+  }
+  __syncthreads();
+  if (tid < MM) {
+    const int i = tid / M, m = tid % M;
+    const double2 p = sh.P[m][i];
+    sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
+  }
+  __syncthreads();
+
+  for (int it = 0; it < a.iters; ++it) {
+    const bool last = (it == a.iters - 1);
+    if (last) {  // parameters of iteration L-1, used by Algorithm 1's output
+      if (tid < MM) a.P_prev[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
+      if (tid < M) a.lam_prev[(size_t)f * M + tid] = sh.lam64[tid];
+      if (tid == 0) a.logdetS2_prev[f] = sh.logdetS2;
+    }
+    float acc[VP];
+#pragma unroll
+    for (int j = 0; j < VP; ++j) acc[j] = 0.f;
+    float2 ph[kHoist ? M : 1][kHoist ? M : 1];
+    float lamr[M], ilamr[M];
+    if constexpr (kHoist) {
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m) ph[i][m] = sh.PH[i][m];
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      lamr[i] = sh.lam[i];
+      ilamr[i] = sh.ilam[i];
+    }
+
+    for (int n = tid; n < N; n += NT) {
+      float2 yv[M];
+      load_bin<M, ST>(ysrc + (size_t)n * M, yv);
+      const float v1 = v1p[n], v2 = v2p[n];
+      if (last) {
+        a.v_prev[fN + n] = v1;
+        a.v_prev[(size_t)F * N + fN + n] = v2;
+      }
+      float2 yt[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        float2 s;
+        if constexpr (kHoist) {
+          s = cmul(ph[i][0], yv[0]);
+#pragma unroll
+          for (int m = 1; m < M; ++m) s = cfma(ph[i][m], yv[m], s);
+        } else {
+          s = cmul(sh.PH[i][0], yv[0]);
+#pragma unroll
+          for (int m = 1; m < M; ++m) s = cfma(sh.PH[i][m], yv[m], s);
+        }
+        yt[i] = s;
+      }
+      float ca[M], cb[M], cc[M];
+      float s1 = 0.f, s2 = 0.f, ql = 0.f;
+      LogProd lp;
+      const float v12 = v1 * v2;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const float e = v1 * lamr[i];
+        const float d = e + v2;
+        const float r = __fdividef(1.f, d);
+        const float p = cabs2(yt[i]);
+        ca[i] = e * r;        // mut1_i = ca_i yt_i
+        cb[i] = v2 * r;       // mut2_i = cb_i yt_i
+        cc[i] = v2 * ca[i];   // v1 v2 lam_i / d_i
+        s1 = fmaf(ca[i] * ca[i] * p, ilamr[i], fmaf(v12, r, s1));  // (|mut1|^2 + c) / lam
+        s2 = fmaf(cb[i] * cb[i], p, s2 + cc[i]);                   // |mut2|^2 + c
+        ql = fmaf(p, r, ql);
+        lp.mul(d);
+      }
+      const float lg = lp.log();  // sum_i log d_i
+      const float v1n = fmaxf(s1 * (1.f / M), vf);
+      const float v2n = fmaxf(s2 * (1.f / M), vf);
+      v1p[n] = v1n;
+      v2p[n] = v2n;
+      const float r1 = rsqrtf(v1n), r2 = rsqrtf(v2n);
+      const float w1 = r1 * r1, w2 = r2 * r2;
+      float2 u[M], t[M];  // mut_j / sqrt(v_j')
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        u[i] = cscale(yt[i], ca[i] * r1);
+        t[i] = cscale(yt[i], cb[i] * r2);
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        acc[i] += fmaf(cc[i], w1, cabs2(u[i]));
+        acc[MM + i] += fmaf(cc[i], w2, cabs2(t[i]));
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) {
+          const int o = M + 2 * pair_index(M, i, k);
+          const float2 zu = cmulc(u[i], u[k]);
+          const float2 zt = cmulc(t[i], t[k]);
+          acc[o] += zu.x;
+          acc[o + 1] += zu.y;
+          acc[MM + o] += zt.x;
+          acc[MM + o + 1] += zt.y;
+        }
+      acc[2 * MM] += lg;
+      acc[2 * MM + 1] += ql;
+    }
+
+    warp_transpose_reduce<VP>(acc, lane);
+#pragma unroll
+    for (int j = 0; j < KP; ++j) sh.red[warp][KP * lane + j] = acc[j];
+    __syncthreads();
+    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s[w & 3] += (double)sh.red[w][i];
+      sh.tot[i] = (s[0] + s[1]) + (s[2] + s[3]);
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+      const double invN = 1.0 / (double)N;
+      if (lane == 0) {
+        const double ll = -(double)N * M * 1.1447298858494002 - sh.tot[2 * MM] -
+                          sh.tot[2 * MM + 1] - (double)N * sh.logdetS2;
+        a.llf[(size_t)it * F + f] = ll;
+        if (!isfinite(ll)) {
+          set_status(a.status, kErrNonFinite);
+          sh.fail = kErrNonFinite;
+        }
+      }
+      for (int e = lane; e < MM; e += 32) {  // St_j = sums / N, Hermitian
+        const int i = e / M, j = e % M;
+        float2 s1v, s2v;
+        if (i == j) {
+          s1v = make_float2((float)(sh.tot[i] * invN), 0.f);
+          s2v = make_float2((float)(sh.tot[MM + i] * invN), 0.f);
+        } else {
+          const int lo = min(i, j), hi = max(i, j);
+          const int o = M + 2 * pair_index(M, lo, hi);
+          const float sg = (i < j) ? 1.f : -1.f;
+          s1v = make_float2((float)(sh.tot[o] * invN), sg * (float)(sh.tot[o + 1] * invN));
+          s2v = make_float2((float)(sh.tot[MM + o] * invN), sg * (float)(sh.tot[MM + o + 1] * invN));
+        }
+        sh.la.A[i][j] = s1v;
+        sh.la.L[i][j] = s2v;
+      }
+      __syncwarp();
+      double ldQ = 0.0;
+      const int rc = warp_gevd<M>(sh.la, lane, sh.sig, &ldQ);
+      if (rc != kOk) {
+        if (lane == 0) {
+          set_status(a.status, rc);
+          sh.fail = rc;
+        }
+      } else {
+        warp_update_basis<M>(sh.P, sh.la, lane);
+        if (lane < M) {
+          sh.lam64[lane] = (double)sh.sig[lane];
+          sh.lam[lane] = sh.sig[lane];
+          sh.ilam[lane] = 1.f / sh.sig[lane];
+        }
+        if (lane == 0) sh.logdetS2 -= ldQ;  // log det S2 = -log|det P|^2, P <- P Q
+        for (int e = lane; e < MM; e += 32) {
+          const int i = e / M, m = e % M;
+          const double2 p = sh.P[m][i];
+          sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
+        }
+      }
+    }
+    __syncthreads();
+    if (sh.fail) break;
+  }
+
+  if (tid < MM) a.P[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
+  if (tid < M) a.lam[(size_t)f * M + tid] = sh.lam64[tid];
+  if (tid == 0) a.logdetS2[f] = sh.logdetS2;
+  if (res) {
+    for (int n = tid; n < N; n += NT) {
+      vg1[n] = vs[n];
+      vg2[n] = vs[N + n];
+    }
+  }
+}
+
+// Posterior means in the original basis (Algorithm 1, last step): mu1 = P^-H (a .* yt),
+// a_i = v1 lam_i / (v1 lam_i + v2); mu2 = y - mu1 (y = x1 + x2, Sec. 2).
+template <int M, int ST>
+__global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
+  using E = typename Elem<ST>::T;
+  __shared__ float2 PH[M][M], PiH[M][M];
+  __shared__ float lam[M];
+  const int f = blockIdx.y, tid = threadIdx.x;
+  const size_t MM = (size_t)M * M;
+  if (tid < M * M) {
+    PH[tid / M][tid % M] = a.PH[f * MM + tid];
+    PiH[tid / M][tid % M] = a.PinvH[f * MM + tid];
+  }
+  if (tid < M) lam[tid] = a.lam[(size_t)f * M + tid];
+  __syncthreads();
+  const int n = blockIdx.x * 256 + tid;
+  if (n >= a.N) return;
+  const size_t b = (size_t)f * a.N + n;
+  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+  float2 yv[M];
+  load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + b * M, yv);
+  const float v1 = a.v[b], v2 = a.v[(size_t)a.F * a.N + b];
+  float2 mt[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 s = cmul(PH[i][0], yv[0]);
+#pragma unroll
+    for (int m = 1; m < M; ++m) s = cfma(PH[i][m], yv[m], s);
+    const float e = v1 * lam[i];
+    mt[i] = cscale(s, e / (e + v2));
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 s = cmul(PiH[i][0], mt[0]);
+#pragma unroll
+    for (int m = 1; m < M; ++m) s = cfma(PiH[i][m], mt[m], s);
+    a.x1[b * M + i] = s;
+    a.x2[b * M + i] = csub(cscale(yv[i], gi), s);
+  }
+}
+
+// ------------------------------------------------------------------ host-side launchers
+int em_threads(int M, int N) { return (N <= 384) ? 128 : 256; }
+
+size_t em_dyn_smem(int M, int storage, int N) {
+  const size_t esz = storage ? 4 : 8;
+  return (((size_t)N * M * esz + 15) & ~(size_t)15) + 8 * (size_t)N;
+}
+
+bool em_resident(int M, int storage, int N) { return em_dyn_smem(M, storage, N) <= 100 * 1024; }
+
+template <int M, int ST, int NT>
+static cudaError_t launch_fast_t(const FastEmArgs& a0, cudaStream_t st) {
+  FastEmArgs a = a0;
+  size_t dyn = 0;
+  if (a.resident) dyn = em_dyn_smem(M, ST, a.N);
+  auto k = fast_em_kernel<M, ST, NT>;
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<a.F, NT, dyn, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int M, int ST>
+static cudaError_t launch_fast_m(const FastEmArgs& a, cudaStream_t st) {
+  return em_threads(M, a.N) == 128 ? launch_fast_t<M, ST, 128>(a, st) : launch_fast_t<M, ST, 256>(a, st);
+}
+
+template <int ST>
+static cudaError_t launch_fast_s(int M, const FastEmArgs& a, cudaStream_t st) {
+  switch (M) {
+    case 1: return launch_fast_m<1, ST>(a, st);
+    case 2: return launch_fast_m<2, ST>(a, st);
+    case 3: return launch_fast_m<3, ST>(a, st);
+    case 4: return launch_fast_m<4, ST>(a, st);
+    case 5: return launch_fast_m<5, ST>(a, st);
+    case 6: return launch_fast_m<6, ST>(a, st);
+    case 7: return launch_fast_m<7, ST>(a, st);
+    case 8: return launch_fast_m<8, ST>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fast_em(int M, int storage, const FastEmArgs& a, cudaStream_t st) {
+  return storage ? launch_fast_s<1>(M, a, st) : launch_fast_s<0>(M, a, st);
+}
+
+template <int M, int ST>
+static cudaError_t launch_sep_fast_m(const SepFastArgs& a, cudaStream_t st) {
+  dim3 grid((a.N + 255) / 256, a.F);
+  sep_fast_kernel<M, ST><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_sep_fast_s(int M, const SepFastArgs& a, cudaStream_t st) {
+  switch (M) {
+    case 1: return launch_sep_fast_m<1, ST>(a, st);
+    case 2: return launch_sep_fast_m<2, ST>(a, st);
+    case 3: return launch_sep_fast_m<3, ST>(a, st);
+    case 4: return launch_sep_fast_m<4, ST>(a, st);
+    case 5: return launch_sep_fast_m<5, ST>(a, st);
+    case 6: return launch_sep_fast_m<6, ST>(a, st);
+    case 7: return launch_sep_fast_m<7, ST>(a, st);
+    case 8: return launch_sep_fast_m<8, ST>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sep_fast(int M, int storage, const SepFastArgs& a, cudaStream_t st) {
+  return storage ? launch_sep_fast_s<1>(M, a, st) : launch_sep_fast_s<0>(M, a, st);
+}
+
+}  // namespace fca

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libfca.so (include/fca.h), same names as the C ABI.
+
+Argument marshalling only: every step of the EM runs in the library's CUDA kernels. Tensors
+are torch tensors (device tensors, or host tensors -- pinned for asynchronous copies); the
+binding passes their data pointers and the CUDA stream handle. If the compiled library is
+missing this module raises at import: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfca.so")
+
+FCA_OK = 0
+FCA_STORE_C64, FCA_STORE_F16_SCALED = 0, 1
+FCA_MEM_DEVICE, FCA_MEM_HOST = 0, 1
+FCA_SEP_ALG1, FCA_SEP_FINAL_PARAMS = 0, 1
+STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NOMEM",
+                4: "FCA_ERR_NOT_PD", 5: "FCA_ERR_EIG_NOCONV", 6: "FCA_ERR_NONFINITE",
+                7: "FCA_ERR_TIMEOUT", 8: "FCA_ERR_STATE"}
+
+# Every entry point declared in include/fca.h.
+EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
+           "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_kernel_launches",
+           "fca_sync_status", "fca_free", "fca_status_string", "fca_version")
+
+
+class fca_problem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("location", ctypes.c_int32),
+                ("y", ctypes.c_void_p), ("y_scale", ctypes.c_void_p),
+                ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p)]
+
+
+class FCAError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} ({fca_status_string(code)})")
+
+
+def _load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libfca.so not built at {path}: run paper_1805_06572_gb300/build.py "
+                          "(the FCA kernels have no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    V, I = ctypes.c_void_p, ctypes.c_int32
+    lib.fca_init.argtypes = [ctypes.POINTER(fca_problem), V, ctypes.POINTER(V)]
+    lib.fca_load.argtypes = [V, ctypes.POINTER(fca_problem), V]
+    lib.fca_em_conventional.argtypes = [V, I, V, V]
+    lib.fca_em_fast.argtypes = [V, I, V, V]
+    lib.fca_separate.argtypes = [V, V, V, I, V]
+    lib.fca_get_params.argtypes = [V, V, V, V]
+    lib.fca_loglik_bins.argtypes = [V, V, ctypes.POINTER(I), V]
+    lib.fca_last_em_kernel_ms.argtypes = [V, ctypes.POINTER(ctypes.c_float)]
+    lib.fca_kernel_launches.argtypes = []
+    lib.fca_kernel_launches.restype = ctypes.c_uint64
+    lib.fca_sync_status.argtypes = [V, V]
+    lib.fca_free.argtypes = [V]
+    lib.fca_free.restype = None
+    lib.fca_status_string.argtypes = [ctypes.c_int]
+    lib.fca_status_string.restype = ctypes.c_char_p
+    lib.fca_version.argtypes = []
+    lib.fca_version.restype = ctypes.c_char_p
+    for name in ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
+                 "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_sync_status"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def fca_status_string(code: int) -> str:
+    return lib.fca_status_string(int(code)).decode()
+
+
+def fca_version() -> str:
+    return lib.fca_version().decode()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check(rc: int, where: str):
+    if rc != FCA_OK:
+        raise FCAError(rc, where)
+
+
+def _problem(y, v0, S0, y_scale):
+    if y.dtype == torch.complex64:
+        F, N, M = y.shape
+        storage = FCA_STORE_C64
+    elif y.dtype == torch.float16:
+        F, N, M, two = y.shape
+        assert two == 2
+        storage = FCA_STORE_F16_SCALED
+    else:
+        raise TypeError("y must be complex64 [F,N,M] or float16 [F,N,M,2]")
+    for t in (y, v0, S0) + ((y_scale,) if y_scale is not None else ()):
+        if not t.is_contiguous():
+            raise ValueError("inputs must be contiguous")
+        if t.is_cuda != y.is_cuda:
+            raise ValueError("y, y_scale, v0 and S0 must all be on the device or all on the host")
+    if v0.dtype != torch.float64 or S0.dtype != torch.complex128:
+        raise TypeError("v0 must be float64 [2,F,N], S0 complex128 [2,F,M,M]")
+    p = fca_problem(M=M, F=F, N=N, storage=storage,
+                    location=FCA_MEM_DEVICE if y.is_cuda else FCA_MEM_HOST,
+                    y=y.data_ptr(), y_scale=None if y_scale is None else y_scale.data_ptr(),
+                    v0=v0.data_ptr(), S0=S0.data_ptr())
+    return p
+
+
+class State:
+    """Owning handle of an fca_state (freed by fca_free or garbage collection)."""
+
+    def __init__(self, handle: int, M: int, F: int, N: int, storage: int):
+        self.handle, self.M, self.F, self.N, self.storage = handle, M, F, N, storage
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.fca_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def fca_init(y, v0, S0, y_scale=None, stream=None) -> State:
+    p = _problem(y, v0, S0, y_scale)
+    out = ctypes.c_void_p()
+    _check(lib.fca_init(ctypes.byref(p), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "fca_init")
+    return State(out.value, p.M, p.F, p.N, p.storage)
+
+
+def fca_load(state: State, y, v0, S0, y_scale=None, stream=None):
+    p = _problem(y, v0, S0, y_scale)
+    _check(lib.fca_load(ctypes.c_void_p(state.handle), ctypes.byref(p), ctypes.c_void_p(_stream(stream))),
+           "fca_load")
+
+
+def fca_em_fast(state: State, iters: int, loglik=None, stream=None):
+    _check(lib.fca_em_fast(ctypes.c_void_p(state.handle), int(iters), _ptr(loglik),
+                           ctypes.c_void_p(_stream(stream))), "fca_em_fast")
+
+
+def fca_em_conventional(state: State, iters: int, loglik=None, stream=None):
+    _check(lib.fca_em_conventional(ctypes.c_void_p(state.handle), int(iters), _ptr(loglik),
+                                   ctypes.c_void_p(_stream(stream))), "fca_em_conventional")
+
+
+def fca_separate(state: State, x1, x2, mode: int = FCA_SEP_ALG1, stream=None):
+    _check(lib.fca_separate(ctypes.c_void_p(state.handle), _ptr(x1), _ptr(x2), int(mode),
+                            ctypes.c_void_p(_stream(stream))), "fca_separate")
+
+
+def fca_get_params(state: State, v=None, S=None, stream=None):
+    """v: device float32 [2,F,N] or None; S: host complex128 [2,F,M,M] or None."""
+    _check(lib.fca_get_params(ctypes.c_void_p(state.handle), _ptr(v), _ptr(S),
+                              ctypes.c_void_p(_stream(stream))), "fca_get_params")
+
+
+def fca_loglik_bins(state: State, stream=None):
+    """Per-frequency log-likelihood [L, F] (float64, host) of the last EM call."""
+    n = ctypes.c_int32(0)
+    _check(lib.fca_loglik_bins(ctypes.c_void_p(state.handle), None, ctypes.byref(n),
+                               ctypes.c_void_p(_stream(stream))), "fca_loglik_bins")
+    out = torch.empty((n.value, state.F), dtype=torch.float64).pin_memory()
+    _check(lib.fca_loglik_bins(ctypes.c_void_p(state.handle), _ptr(out), None,
+                               ctypes.c_void_p(_stream(stream))), "fca_loglik_bins")
+    return out
+
+
+def fca_last_em_kernel_ms(state: State) -> float:
+    ms = ctypes.c_float(0.0)
+    _check(lib.fca_last_em_kernel_ms(ctypes.c_void_p(state.handle), ctypes.byref(ms)),
+           "fca_last_em_kernel_ms")
+    return float(ms.value)
+
+
+def fca_kernel_launches() -> int:
+    return int(lib.fca_kernel_launches())
+
+
+def fca_sync_status(state: State, stream=None) -> int:
+    return int(lib.fca_sync_status(ctypes.c_void_p(state.handle), ctypes.c_void_p(_stream(stream))))
+
+
+def fca_free(state: State):
+    if state.handle:
+        lib.fca_free(ctypes.c_void_p(state.handle))
+        state.handle = None
+
+
+def run(y, v0, S0, iters: int, form: str = "fast", y_scale=None, mode: int = FCA_SEP_ALG1,
+        want_ll: bool = True, stream=None):
+    """One-shot convenience over the C ABI: load, `iters` EM iterations, posterior means.
+
+    Inputs may be device tensors or (pinned) host tensors. Returns device tensors
+    (x1, x2, loglik, v) and the state."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = fca_init(y, v0, S0, y_scale=y_scale, stream=stream)
+    ll = torch.empty(iters, dtype=torch.float64, device=dev) if want_ll and iters > 0 else None
+    (fca_em_fast if form == "fast" else fca_em_conventional)(st, iters, ll, stream=stream)
+    x1 = torch.empty((st.F, st.N, st.M), dtype=torch.complex64, device=dev)
+    x2 = torch.empty_like(x1)
+    fca_separate(st, x1, x2, mode, stream=stream)
+    v = torch.empty((2, st.F, st.N), dtype=torch.float32, device=dev)
+    fca_get_params(st, v=v, stream=stream)
+    return x1, x2, ll, v, st

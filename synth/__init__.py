@@ -13,8 +13,14 @@ Recipe (all in FP64 NumPy, PCG64 streams, cast to complex64 at the end):
   * z ~ CN(0, I_M) drawn as [2][F][N][M]; x_k = sqrt(v_k) chol(R_k) z_k; y = x1 + x2.
 CN(0, 1) means real and imaginary parts each N(0, 1/2) (the pi^-M density of Eq. (like)).
 
-Initial parameters: b_j(f) ~ CN(0, I_M) from PCG64(seed + 1000 + j),
-S_j^(0)(f) = b_j b_j^H + I and v_j^(0)(n, f) = max(|y(n,f)|^2, eps_f) / (2 tr S_j^(0)(f)),
+Initial parameters (Algorithm 1 leaves them to the user; the paper's experiment estimates
+the spatial covariances from time-frequency masks). Two recipes:
+  * "mask" (default): a stand-in for a mask-based estimate. The ideal binary mask
+    m_1(n,f) = [|x_1(n,f)|^2 > |x_2(n,f)|^2], m_2 = 1 - m_1, taken from the generator's source
+    images, gives S_j^(0)(f) = mean over {n : m_j = 1} of M y y^H / |y|^2, plus 0.01 I
+    (I when the mask is empty), and v_j^(0)(n,f) = max(|y|^2, eps_f) (0.1 + 0.8 m_j) / tr S_j^(0);
+  * "random": b_j(f) ~ CN(0, I_M) from PCG64(seed + 1000 + j), S_j^(0)(f) = b_j b_j^H + I and
+    v_j^(0)(n, f) = max(|y(n,f)|^2, eps_f) / (2 tr S_j^(0)(f)).
 eps_f = 1e-12 mean_n |y(n,f)|^2.
 """
 from __future__ import annotations
@@ -72,8 +78,13 @@ def make_mixture(M: int, F: int, N: int, delta: float, sigma: float, seed: int):
     return {"y": y, "R": R, "v": v, "x": x.astype(np.complex64)}
 
 
-def init_params(y: np.ndarray, seed: int):
-    """Initial (v0 [2][F][N] float64, S0 [2][F][M][M] complex128) for mixture y [F][N][M]."""
+def init_params(y: np.ndarray, seed: int, x: np.ndarray | None = None, recipe: str | None = None):
+    """Initial (v0 [2][F][N] float64, S0 [2][F][M][M] complex128) for mixture y [F][N][M].
+    recipe "mask" needs the source images x [2][F][N][M]; the default is "mask" when x is
+    given, else "random"."""
+    recipe = recipe or ("mask" if x is not None else "random")
+    if recipe == "mask":
+        return _mask_init(y, x)
     F, N, M = y.shape
     yd = y.astype(np.complex128)
     S0 = np.empty((2, F, M, M), np.complex128)
@@ -85,6 +96,28 @@ def init_params(y: np.ndarray, seed: int):
     eps = 1e-12 * pw.mean(axis=1, keepdims=True)
     tr = np.real(np.einsum("kfii->kf", S0))                             # [2][F]
     v0 = np.maximum(pw, eps)[None] / (2.0 * tr[:, :, None])
+    return v0, S0
+
+
+def _mask_init(y: np.ndarray, x: np.ndarray):
+    F, N, M = y.shape
+    yd = y.astype(np.complex128)
+    xd = x.astype(np.complex128)
+    px = np.sum(np.abs(xd) ** 2, axis=3)                                 # [2][F][N]
+    m1 = (px[0] > px[1]).astype(np.float64)
+    masks = np.stack([m1, 1.0 - m1])
+    pw = np.sum(np.abs(yd) ** 2, axis=2)                                # [F][N]
+    eps = 1e-12 * pw.mean(axis=1, keepdims=True)
+    wn = M / np.maximum(pw, np.where(pw > 0, 0.0, 1.0))                 # M / |y|^2 (0 for y = 0)
+    wn = np.where(pw > 0, wn, 0.0)
+    S0 = np.empty((2, F, M, M), np.complex128)
+    for j in range(2):
+        cnt = masks[j].sum(axis=1)
+        S = np.einsum("fn,fni,fnj->fij", masks[j] * wn, yd, yd.conj())
+        S = S / np.maximum(cnt, 1.0)[:, None, None] + 0.01 * np.eye(M)
+        S0[j] = np.where((cnt > 0)[:, None, None], S, np.eye(M))
+    tr = np.real(np.einsum("kfii->kf", S0))
+    v0 = np.maximum(pw, eps)[None] * (0.1 + 0.8 * masks) / tr[:, :, None]
     return v0, S0
 
 
@@ -104,10 +137,10 @@ def quantize_f16(y: np.ndarray):
     return y16, g, deq
 
 
-def make_config(name: str, mixture_index: int = 0, F: int | None = None):
+def make_config(name: str, mixture_index: int = 0, F: int | None = None, recipe: str = "mask"):
     """Mixture + initial params for a named workload (optionally with fewer bins)."""
     c = CONFIGS[name]
     seed = config_seed(name, mixture_index)
     mix = make_mixture(c.M, F or c.F, c.N, c.delta, c.sigma, seed)
-    v0, S0 = init_params(mix["y"], seed)
+    v0, S0 = init_params(mix["y"], seed, x=mix["x"], recipe=recipe)
     return c, mix, v0, S0
