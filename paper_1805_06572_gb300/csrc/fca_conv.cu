@@ -21,9 +21,8 @@ namespace fca {
 template <int M, int NW>
 struct ConvShared {
   static constexpr int V = 2 * M * M + 2;
-  static constexpr int VP = (V + 31) / 32 * 32;
-  float red[NW][VP];
-  double tot[VP];
+  float red[NW][V];
+  double tot[V];
   double2 S[2][kMaxM][kMaxM];
   float2 S32[2][M][M];
   float2 Si32[2][M][M];
@@ -70,12 +69,15 @@ __device__ bool warp_hpd_inverse(WarpLA& la, const double2 (*S)[kMaxM], float2 (
   return true;
 }
 
+__host__ __device__ constexpr int conv_min_blocks(int M) { return M <= 3 ? 4 : (M <= 4 ? 3 : 2); }
+
 template <int M, int ST, int NT>
-__global__ void __launch_bounds__(NT) conv_em_kernel(const ConvEmArgs a) {
+__global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const ConvEmArgs a) {
   using E = typename Elem<ST>::T;
   constexpr int NW = NT / 32;
   using Sh = ConvShared<M, NW>;
-  constexpr int V = Sh::V, VP = Sh::VP, KP = VP / 32;
+  constexpr int V = Sh::V;
+  using RS = RedShape<V>;
   constexpr int MM = M * M;
   __shared__ Sh sh;
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -138,9 +140,9 @@ __global__ void __launch_bounds__(NT) conv_em_kernel(const ConvEmArgs a) {
     __syncthreads();
     if (sh.fail) break;
 
-    float acc[VP];
+    float acc[RS::NA];
 #pragma unroll
-    for (int j = 0; j < VP; ++j) acc[j] = 0.f;
+    for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
     int bad = 0;
     for (int n = tid; n < N; n += NT) {
       float2 yv[M];
@@ -279,15 +281,17 @@ __global__ void __launch_bounds__(NT) conv_em_kernel(const ConvEmArgs a) {
       }
     }
 
-    warp_transpose_reduce<VP>(acc, lane);
-#pragma unroll
-    for (int j = 0; j < KP; ++j) sh.red[warp][KP * lane + j] = acc[j];
+    warp_reduce_store<V>(acc, lane, sh.red[warp]);
     __syncthreads();
-    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps
-      double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps (pairwise)
+      double s[NW];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s[w & 3] += (double)sh.red[w][i];
-      sh.tot[i] = (s[0] + s[1]) + (s[2] + s[3]);
+      for (int w = 0; w < NW; ++w) s[w] = (double)sh.red[w][i];
+#pragma unroll
+      for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+        for (int w = 0; w < h; ++w) s[w] += s[w + h];
+      sh.tot[i] = s[0];
     }
     __syncthreads();
     const double invN = 1.0 / (double)N;
@@ -396,8 +400,11 @@ template <int M, int ST, int NT>
 static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
   size_t dyn = a.resident ? em_dyn_smem(M, ST, a.N) : 0;
   auto k = conv_em_kernel<M, ST, NT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   if (dyn > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
   k<<<a.F, NT, dyn, st>>>(a);

@@ -135,7 +135,7 @@ struct LogProd {
 // acc[0..VP) holds this lane's partial sums (VP a multiple of 32). Afterwards lane l holds,
 // in acc[0..VP/32), the warp-wide sums of values [l*VP/32, (l+1)*VP/32).
 template <int VP>
-__device__ __forceinline__ void warp_transpose_reduce(float (&acc)[VP], int lane) {
+__device__ __forceinline__ void warp_transpose_reduce(float* acc, int lane) {
   static_assert(VP % 32 == 0, "VP must be a multiple of 32");
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
@@ -148,6 +148,39 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&acc)[VP], int lane
       float keep = up ? acc[j + h] : acc[j];
       acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
+  }
+}
+
+// Shape of the per-lane partial-sum vector for V values: VT values go through the transpose
+// reduction (a multiple of 32) and the last VR (at most 4) through plain butterflies, which is
+// cheaper than padding a short tail to 32.
+template <int V>
+struct RedShape {
+  static constexpr int kTail = V % 32;
+  static constexpr int VT = (kTail <= 4) ? V - kTail : V - kTail + 32;
+  static constexpr int VR = (kTail <= 4) ? kTail : 0;
+  static constexpr int KP = VT / 32;     // transposed values held per lane after the reduction
+  static constexpr int NA = VT + VR;     // length of the accumulator array
+};
+
+// Reduce acc[0..NA) over the warp and store the warp's V sums to out[0..V) (shared memory).
+template <int V>
+__device__ __forceinline__ void warp_reduce_store(float* acc, int lane, float* out) {
+  using RS = RedShape<V>;
+  if constexpr (RS::VR > 0) {
+#pragma unroll
+    for (int j = 0; j < RS::VR; ++j) {
+      float x = acc[RS::VT + j];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[RS::VT + j] = x;
+    }
+  }
+  if constexpr (RS::VT > 0) {
+    warp_transpose_reduce<RS::VT>(acc, lane);
+#pragma unroll
+    for (int j = 0; j < RS::KP; ++j)
+      if (RS::KP * lane + j < V) out[RS::KP * lane + j] = acc[j];
   }
 }
 
@@ -183,8 +216,9 @@ __device__ bool warp_cholesky(WarpLA& la, int lane) {
       __syncwarp();
       return false;
     }
-    const float lkk = sqrtf(bkk);
-    const float il = 1.0f / lkk;
+    float il = rsqrtf(bkk);
+    il = il * fmaf(-0.5f * bkk * il, il, 1.5f);  // Newton step: 1/sqrt(bkk) to rounding
+    const float lkk = bkk * il;
     __syncwarp();
     if (lane == k) {
       la.L[k][k] = make_float2(lkk, 0.f);
@@ -254,6 +288,7 @@ __device__ int warp_jacobi(WarpLA& la, int lane, float tol, int max_sweeps) {
   const float tol2 = tol * tol;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
+    float worst = 0.f;  // largest |a_pq|^2 / |a_pp a_qq| met in this sweep
     for (int r = 0; r < n - 1; ++r) {
       if (lane < n / 2) {
         const int k = lane;
@@ -266,13 +301,23 @@ __device__ int warp_jacobi(WarpLA& la, int lane, float tol, int max_sweeps) {
           const float app = la.A[p][p].x, aqq = la.A[q][q].x;
           const float2 apq = la.A[p][q];
           const float r2 = cabs2(apq);
-          if (r2 > tol2 * fabsf(app * aqq) && r2 > 1e-36f) {
-            const float rr = sqrtf(r2);
-            const float tau = (aqq - app) / (2.f * rr);
-            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-            c = 1.0f / sqrtf(fmaf(t, t, 1.f));  // correctly rounded: |det J| stays close to 1
+          const float den = fabsf(app * aqq);
+          if (r2 > tol2 * den && r2 > 1e-36f) {
+            worst = fmaxf(worst, den > 0.f ? __fdividef(r2, den) : 1.f);
+            // 1/|a_pq| and c = 1/sqrt(1+t^2) each get one Newton step after the approximate
+            // reciprocal square root, so that |e| = 1 and c^2 + s^2 = 1 hold to rounding:
+            // a biased error there would make U non-unitary in the same direction every
+            // rotation and shift the scale of the implied S2.
+            float ir = rsqrtf(r2);
+            ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);   // 1 / |a_pq|
+            const float tau = 0.5f * (aqq - app) * ir;
+            const float h = fmaf(tau, tau, 1.f);
+            const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
+            const float g = fmaf(t, t, 1.f);
+            c = rsqrtf(g);
+            c = c * fmaf(-0.5f * g * c, c, 1.5f);
             s = t * c;
-            e = cscale(apq, 1.f / rr);
+            e = cscale(apq, ir);
             rotated = 1;
           }
           // J_pp = c, J_qp = -s conj(e), J_pq = s, J_qq = c conj(e)
@@ -320,7 +365,13 @@ __device__ int warp_jacobi(WarpLA& la, int lane, float tol, int max_sweeps) {
       }
       __syncwarp();
     }
+    // Stop when nothing rotated, or when every rotation of this sweep started from a relative
+    // off-diagonal below 1e-4: cyclic Jacobi converges quadratically, so the next sweep would
+    // meet off-diagonals of order 1e-8 and rotate nothing.
     if (!__any_sync(0xffffffffu, rotated)) return sweep + 1;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if (worst <= 1e-8f) return sweep + 1;
   }
   return -1;
 }
@@ -353,13 +404,15 @@ __device__ void warp_backsolve_LH(WarpLA& la, int lane) {
 // la.A (A) and la.L (B): Cholesky B = L L^H, W = L^-1 A L^-H = U Sig U^H (Jacobi),
 // Q = L^-H U, so that Q^H B Q = I and Q^H A Q = Sig (Eq. (GEVDeff5)). On return la.V = Q and
 // sig[i] = Sig_ii. *logdetQ receives log|det Q|^2 of the Q actually returned:
-// -log det B + log|det U|^2, where the FP32 rotations leave U unitary only to rounding, so
+// 2 sum_i log(1/L_ii) + log|det U|^2, where the FP32 rotations leave U unitary only to
+// rounding, so
 // log|det U|^2 = log det(U^H U) = ||U||_F^2 - M to first order in U^H U - I (FP64 sum).
 // Returns a device status code.
 template <int M>
 __device__ int warp_gevd(WarpLA& la, int lane, float* sig, double* logdetQ) {
   if (!warp_cholesky<M>(la, lane)) return kErrNotPD;
-  float ld = (lane < M) ? 2.f * logf(la.L[lane][lane].x) : 0.f;
+  // log|det L^-H|^2 from the reciprocal pivots the solves below actually apply.
+  float ld = (lane < M) ? 2.f * logf(la.invd[lane]) : 0.f;
   ld = warp_sum(ld);
   warp_congruence_inv<M>(la, lane);
   const int sw = warp_jacobi<M>(la, lane, 2.0e-7f, 30);
@@ -374,7 +427,7 @@ __device__ int warp_gevd(WarpLA& la, int lane, float* sig, double* logdetQ) {
   for (int o = 16; o >= 1; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
   warp_backsolve_LH<M>(la, lane);
   __syncwarp();
-  *logdetQ = (un - (double)M) - (double)ld;
+  *logdetQ = (un - (double)M) + (double)ld;
   for (int i = 0; i < M; ++i) {
     const float s = sig[i];
     if (!(s > 0.f) || !(s < 3.0e38f)) return kErrNotPD;

@@ -18,7 +18,9 @@
 //     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use).
 // The log-likelihood of iteration l uses log det Rx = sum_i log d_i + log det S2 and
 // y^H Rx^-1 y = sum_i |yt_i|^2 / d_i, which follow from Rx = P^-H (v1 Lam + v2 I) P^-1.
-// The mixture and v stay in shared memory across iterations when they fit.
+// The mixture and v stay in shared memory across iterations when they fit. The FP64
+// bookkeeping of an iteration (basis product, log-determinant, log-likelihood) runs in
+// warp 0 after the next basis has been published, overlapping the next bin pass.
 #include "fca_dev.cuh"
 #include "fca_internal.h"
 
@@ -27,16 +29,19 @@ namespace fca {
 template <int M, int NW>
 struct FastShared {
   static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
-  static constexpr int VP = (V + 31) / 32 * 32;
-  float red[NW][VP];
-  double tot[VP];
-  double2 P[kMaxM][kMaxM];
-  float2 PH[M][M];   // FP32 P^H, times the decode scale
+  float red[NW][V];
+  float tot32[V];      // merged sums / N (Gram entries) for the eigensolver
+  double tot[V];       // merged sums in FP64
+  double2 P[kMaxM][kMaxM];  // basis P (FP64)
+  float2 P32[kMaxM][kMaxM]; // P rounded to FP32
+  float2 PH[M][M];     // FP32 P^H (times the decode scale) used by the bin pass
   float lam[M], ilam[M];
   double lam64[kMaxM];
   float sig[kMaxM];
   double logdetS2;
-  int fail;
+  double ldQ;
+  int fail;          // read by every thread after a barrier; written only before one
+  int fail_pending;  // set by the deferred bookkeeping, folded into `fail` by warp 0
   WarpLA la;
 };
 
@@ -44,12 +49,17 @@ __host__ __device__ constexpr int pair_index(int M, int i, int k) {  // i < k
   return i * (M - 1) - i * (i - 1) / 2 + (k - i - 1);
 }
 
+// Resident CTAs per SM the register budget is sized for (one CTA per frequency bin: more
+// CTAs per SM hide each CTA's serial per-bin eigensolver behind the others' bin passes).
+__host__ __device__ constexpr int fast_min_blocks(int M) { return M <= 4 ? 4 : (M <= 6 ? 3 : 2); }
+
 template <int M, int ST, int NT>
-__global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
+__global__ void __launch_bounds__(NT, fast_min_blocks(M)) fast_em_kernel(const FastEmArgs a) {
   using E = typename Elem<ST>::T;
   constexpr int NW = NT / 32;
   using Sh = FastShared<M, NW>;
-  constexpr int V = Sh::V, VP = Sh::VP, KP = VP / 32;
+  constexpr int V = Sh::V;
+  using RS = RedShape<V>;
   constexpr int MM = M * M;
   constexpr bool kHoist = (M <= 4);
   __shared__ Sh sh;
@@ -70,8 +80,13 @@ __global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
   float* v2p = res ? vs + N : vg2;
   const float vf = a.vfloor[f];
   const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+  const double invN = 1.0 / (double)N;
 
-  if (tid < MM) sh.P[tid / M][tid % M] = a.P[(size_t)f * MM + tid];
+  if (tid < MM) {
+    const double2 p = a.P[(size_t)f * MM + tid];
+    sh.P[tid / M][tid % M] = p;
+    sh.P32[tid / M][tid % M] = z2c(p);
+  }
   if (tid < M) {
     const double l = a.lam[(size_t)f * M + tid];
     sh.lam64[tid] = l;
@@ -81,6 +96,7 @@ __global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
   if (tid == 0) {
     sh.logdetS2 = a.logdetS2[f];
     sh.fail = 0;
+    sh.fail_pending = 0;
   }
   if (res) {
     const size_t bytes = (size_t)N * M * sizeof(E);
@@ -104,18 +120,18 @@ __global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
     const double2 p = sh.P[m][i];
     sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
   }
+  if (a.iters == 1) {  // the parameters of iteration L-1 are the initial ones
+    if (tid < MM) a.P_prev[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
+    if (tid < M) a.lam_prev[(size_t)f * M + tid] = sh.lam64[tid];
+    if (tid == 0) a.logdetS2_prev[f] = sh.logdetS2;
+  }
   __syncthreads();
 
   for (int it = 0; it < a.iters; ++it) {
     const bool last = (it == a.iters - 1);
-    if (last) {  // parameters of iteration L-1, used by Algorithm 1's output
-      if (tid < MM) a.P_prev[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
-      if (tid < M) a.lam_prev[(size_t)f * M + tid] = sh.lam64[tid];
-      if (tid == 0) a.logdetS2_prev[f] = sh.logdetS2;
-    }
-    float acc[VP];
+    float acc[RS::NA];
 #pragma unroll
-    for (int j = 0; j < VP; ++j) acc[j] = 0.f;
+    for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
     float2 ph[kHoist ? M : 1][kHoist ? M : 1];
     float lamr[M], ilamr[M];
     if constexpr (kHoist) {
@@ -171,7 +187,6 @@ __global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
         ql = fmaf(p, r, ql);
         lp.mul(d);
       }
-      const float lg = lp.log();  // sum_i log d_i
       const float v1n = fmaxf(s1 * (1.f / M), vf);
       const float v2n = fmaxf(s2 * (1.f / M), vf);
       v1p[n] = v1n;
@@ -201,45 +216,39 @@ __global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
           acc[MM + o] += zt.x;
           acc[MM + o + 1] += zt.y;
         }
-      acc[2 * MM] += lg;
+      acc[2 * MM] += lp.log();
       acc[2 * MM + 1] += ql;
     }
 
-    warp_transpose_reduce<VP>(acc, lane);
-#pragma unroll
-    for (int j = 0; j < KP; ++j) sh.red[warp][KP * lane + j] = acc[j];
+    warp_reduce_store<V>(acc, lane, sh.red[warp]);
     __syncthreads();
-    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps
-      double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps (pairwise)
+      double s[NW];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s[w & 3] += (double)sh.red[w][i];
-      sh.tot[i] = (s[0] + s[1]) + (s[2] + s[3]);
+      for (int w = 0; w < NW; ++w) s[w] = (double)sh.red[w][i];
+#pragma unroll
+      for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+        for (int w = 0; w < h; ++w) s[w] += s[w + h];
+      sh.tot[i] = s[0];
+      sh.tot32[i] = (float)(s[0] * invN);
     }
     __syncthreads();
 
     if (warp == 0) {
-      const double invN = 1.0 / (double)N;
-      if (lane == 0) {
-        const double ll = -(double)N * M * 1.1447298858494002 - sh.tot[2 * MM] -
-                          sh.tot[2 * MM + 1] - (double)N * sh.logdetS2;
-        a.llf[(size_t)it * F + f] = ll;
-        if (!isfinite(ll)) {
-          set_status(a.status, kErrNonFinite);
-          sh.fail = kErrNonFinite;
-        }
-      }
-      for (int e = lane; e < MM; e += 32) {  // St_j = sums / N, Hermitian
+      if (lane == 0 && sh.fail_pending) sh.fail = sh.fail_pending;
+      for (int e = lane; e < MM; e += 32) {  // St_j = sums / N, Hermitian, FP32
         const int i = e / M, j = e % M;
         float2 s1v, s2v;
         if (i == j) {
-          s1v = make_float2((float)(sh.tot[i] * invN), 0.f);
-          s2v = make_float2((float)(sh.tot[MM + i] * invN), 0.f);
+          s1v = make_float2(sh.tot32[i], 0.f);
+          s2v = make_float2(sh.tot32[MM + i], 0.f);
         } else {
           const int lo = min(i, j), hi = max(i, j);
           const int o = M + 2 * pair_index(M, lo, hi);
           const float sg = (i < j) ? 1.f : -1.f;
-          s1v = make_float2((float)(sh.tot[o] * invN), sg * (float)(sh.tot[o + 1] * invN));
-          s2v = make_float2((float)(sh.tot[MM + o] * invN), sg * (float)(sh.tot[MM + o + 1] * invN));
+          s1v = make_float2(sh.tot32[o], sg * sh.tot32[o + 1]);
+          s2v = make_float2(sh.tot32[MM + o], sg * sh.tot32[MM + o + 1]);
         }
         sh.la.A[i][j] = s1v;
         sh.la.L[i][j] = s2v;
@@ -253,23 +262,49 @@ __global__ void __launch_bounds__(NT) fast_em_kernel(const FastEmArgs a) {
           sh.fail = rc;
         }
       } else {
-        warp_update_basis<M>(sh.P, sh.la, lane);
+        // Publish the next basis for the bin pass: P^H <- (P Q)^H from the FP32 copies.
+        for (int e = lane; e < MM; e += 32) {
+          const int i = e / M, m = e % M;  // (P Q)_{m i}
+          float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.la.V[k][i], s);
+          sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
+        }
         if (lane < M) {
-          sh.lam64[lane] = (double)sh.sig[lane];
           sh.lam[lane] = sh.sig[lane];
           sh.ilam[lane] = 1.f / sh.sig[lane];
         }
-        if (lane == 0) sh.logdetS2 -= ldQ;  // log det S2 = -log|det P|^2, P <- P Q
-        for (int e = lane; e < MM; e += 32) {
-          const int i = e / M, m = e % M;
-          const double2 p = sh.P[m][i];
-          sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
-        }
+        if (lane == 0) sh.ldQ = ldQ;
       }
     }
     __syncthreads();
     if (sh.fail) break;
+    if (warp == 0) {
+      // Deferred FP64 bookkeeping (overlaps the other warps' next bin pass): P <- P Q
+      // (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)), the log-likelihood of
+      // this iteration, log det S2 of the next one.
+      warp_update_basis<M>(sh.P, sh.la, lane);
+      for (int e = lane; e < MM; e += 32) sh.P32[e / M][e % M] = z2c(sh.P[e / M][e % M]);
+      if (lane < M) sh.lam64[lane] = (double)sh.sig[lane];
+      if (lane == 0) {
+        const double ll = -(double)N * M * 1.1447298858494002 - sh.tot[2 * MM] -
+                          sh.tot[2 * MM + 1] - (double)N * sh.logdetS2;
+        a.llf[(size_t)it * F + f] = ll;
+        if (!isfinite(ll)) {
+          set_status(a.status, kErrNonFinite);
+          sh.fail_pending = kErrNonFinite;
+        }
+        sh.logdetS2 -= sh.ldQ;  // log det S2 = -log|det P|^2, P <- P Q
+      }
+      __syncwarp();
+      if (it == a.iters - 2) {  // the parameters of iteration L-1
+        for (int e = lane; e < MM; e += 32) a.P_prev[(size_t)f * MM + e] = sh.P[e / M][e % M];
+        if (lane < M) a.lam_prev[(size_t)f * M + lane] = sh.lam64[lane];
+        if (lane == 0) a.logdetS2_prev[f] = sh.logdetS2;
+      }
+    }
   }
+  __syncthreads();
 
   if (tid < MM) a.P[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
   if (tid < M) a.lam[(size_t)f * M + tid] = sh.lam64[tid];
@@ -324,7 +359,7 @@ __global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
 }
 
 // ------------------------------------------------------------------ host-side launchers
-int em_threads(int M, int N) { return (N <= 384) ? 128 : 256; }
+int em_threads(int M, int N) { return 128; }
 
 size_t em_dyn_smem(int M, int storage, int N) {
   const size_t esz = storage ? 4 : 8;
@@ -339,8 +374,11 @@ static cudaError_t launch_fast_t(const FastEmArgs& a0, cudaStream_t st) {
   size_t dyn = 0;
   if (a.resident) dyn = em_dyn_smem(M, ST, a.N);
   auto k = fast_em_kernel<M, ST, NT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   if (dyn > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
   k<<<a.F, NT, dyn, st>>>(a);
