@@ -54,7 +54,8 @@ typedef enum {
   FCA_ERR_EIG_NOCONV = 5,  /* the Jacobi eigensolver hit its sweep cap                    */
   FCA_ERR_NONFINITE = 6,   /* a NaN or infinity appeared in v, S, P or the log-likelihood */
   FCA_ERR_TIMEOUT = 7,     /* a bounded device wait ran out                               */
-  FCA_ERR_STATE = 8        /* the state failed earlier, or the call does not fit its form */
+  FCA_ERR_STATE = 8,       /* the state failed earlier, or the call does not fit its form */
+  FCA_ERR_SCRATCH = 9      /* fca_em_fast_noalloc: the problem needs more than its scratch  */
 } fca_status;
 
 enum { FCA_STORE_C64 = 0, FCA_STORE_F16_SCALED = 1 };
@@ -140,6 +141,43 @@ fca_status fca_last_em_kernel_ms(fca_state* s, float* ms);
 
 /* Number of CUDA kernels this library has launched in this process (all states). */
 uint64_t fca_kernel_launches(void);
+
+/* Size of the fixed device scratch array behind fca_em_fast_noalloc (bytes). */
+#define FCA_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * FastFCA without any device allocation. The paper has no counterpart: this is a way to run
+ * the same kernels for callers that must not allocate device memory once running -- a
+ * real-time audio loop (cudaMalloc / cudaFree may synchronise the device and take unbounded
+ * time) or a host application that hands out device memory only through its own pool.
+ *
+ * Runs the whole job of fca_init + fca_em_fast + fca_separate(FCA_SEP_ALG1) on caller-owned
+ * device buffers (complex64 storage only):
+ *   y_dev       in   complex64 [F][N][M]
+ *   v0_dev      in   double [2][F][N], initial v (clamped to the positivity floor)
+ *   S0_dev      in   complex128 [2][F][M][M], initial S, Hermitian positive definite
+ *   iters       in   number of FastFCA iterations L >= 0
+ *   v_dev       out  float [2][F][N], v after the last iteration
+ *   x1_dev,
+ *   x2_dev      out  complex64 [F][N][M], posterior means of Algorithm 1's output
+ *   loglik_dev  out  NULL or double [iters], as for fca_em_fast
+ * Everything else lives in one file-scope device array of FCA_NOALLOC_SCRATCH_BYTES, which
+ * every GPU that loads the library holds until the process exits. The problem must fit:
+ * 256-byte-aligned regions of 4F (floor) + 2 x (16 F M^2 + 8 F M + 8 F) (basis, eigenvalues,
+ * log-determinants, current and previous) + 8 F max(L, 1) (per-bin log-likelihood) + 8 F N
+ * (previous v) + 16 F M^2 + 4 F M (separation) bytes, plus 256; larger problems return
+ * FCA_ERR_SCRATCH before any work is enqueued (M=4, F=513, N=1000, L=50 needs about 5 MB).
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine). The
+ * first call on a device looks up the array's device address there (cudaGetSymbolAddress,
+ * with that device current) and should come before any stream capture on that device.
+ * All calls share the array, so calls whose work overlaps on the GPU (other host threads,
+ * other streams) race; the call therefore synchronises `cuda_stream` before returning, and
+ * returns the first device-side error of this call (FCA_OK if none).
+ */
+fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const void* y_dev,
+                               const double* v0_dev, const double* S0_dev, int32_t iters,
+                               float* v_dev, void* x1_dev, void* x2_dev, double* loglik_dev,
+                               void* cuda_stream);
 
 /* Static description of a status code. */
 const char* fca_status_string(fca_status st);

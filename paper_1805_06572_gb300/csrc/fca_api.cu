@@ -143,6 +143,8 @@ ParamArgs param_args(fca_state* s) {
 
 }  // namespace
 
+void fca::note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
 extern "C" {
 
 const char* fca_status_string(fca_status st) {
@@ -156,6 +158,7 @@ const char* fca_status_string(fca_status st) {
     case FCA_ERR_NONFINITE: return "non-finite value";
     case FCA_ERR_TIMEOUT: return "device wait timed out";
     case FCA_ERR_STATE: return "state failed earlier or call does not fit its form";
+    case FCA_ERR_SCRATCH: return "problem larger than the no-allocation scratch array";
   }
   return "unknown status";
 }

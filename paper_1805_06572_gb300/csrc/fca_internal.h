@@ -99,6 +99,9 @@ cudaError_t launch_ll_reduce(int F, int iters, const double* llf, double* ll, cu
 // ginv[f] = 1 / g[f].
 cudaError_t launch_invert_scale(int F, const float* g, float* ginv, cudaStream_t st);
 
+// Count n kernel launches in the process-wide counter behind fca_kernel_launches().
+void note_launches(int n);
+
 // Threads per CTA and shared-memory plan of the fused EM kernels (also used by the
 // benchmark's roofline accounting).
 int em_threads(int M, int N);

@@ -21,12 +21,14 @@ FCA_MEM_DEVICE, FCA_MEM_HOST = 0, 1
 FCA_SEP_ALG1, FCA_SEP_FINAL_PARAMS = 0, 1
 STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NOMEM",
                 4: "FCA_ERR_NOT_PD", 5: "FCA_ERR_EIG_NOCONV", 6: "FCA_ERR_NONFINITE",
-                7: "FCA_ERR_TIMEOUT", 8: "FCA_ERR_STATE"}
+                7: "FCA_ERR_TIMEOUT", 8: "FCA_ERR_STATE", 9: "FCA_ERR_SCRATCH"}
+FCA_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 # Every entry point declared in include/fca.h.
 EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
            "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_kernel_launches",
-           "fca_sync_status", "fca_free", "fca_status_string", "fca_version")
+           "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
+           "fca_em_fast_noalloc")
 
 
 class fca_problem(ctypes.Structure):
@@ -63,6 +65,8 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_free.restype = None
     lib.fca_status_string.argtypes = [ctypes.c_int]
     lib.fca_status_string.restype = ctypes.c_char_p
+    lib.fca_em_fast_noalloc.argtypes = [I, I, I, V, V, V, I, V, V, V, V, V]
+    lib.fca_em_fast_noalloc.restype = ctypes.c_int
     lib.fca_version.argtypes = []
     lib.fca_version.restype = ctypes.c_char_p
     for name in ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
@@ -199,6 +203,15 @@ def fca_free(state: State):
     if state.handle:
         lib.fca_free(ctypes.c_void_p(state.handle))
         state.handle = None
+
+
+def fca_em_fast_noalloc(y, v0, S0, iters: int, v, x1, x2, loglik=None, stream=None) -> int:
+    """FastFCA on caller-owned device tensors with the library's fixed scratch array (no
+    device allocation). Synchronises the stream; returns the status code."""
+    F, N, M = y.shape
+    return int(lib.fca_em_fast_noalloc(M, F, N, _ptr(y), _ptr(v0), _ptr(S0), int(iters), _ptr(v),
+                                       _ptr(x1), _ptr(x2), _ptr(loglik),
+                                       ctypes.c_void_p(_stream(stream))))
 
 
 def run(y, v0, S0, iters: int, form: str = "fast", y_scale=None, mode: int = FCA_SEP_ALG1,
