@@ -325,7 +325,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": ach / FP32_PEAK_TFLOPS,
                      "traffic": profiled_traffic("fast_em_kernel_mid.md"),
-                     "kernel": "fast_em_kernel<4,c64,256>", "kernel_ms": 1e3 * kern_fast,
+                     "kernel": "fast_em_kernel<4,c64,128>", "kernel_ms": 1e3 * kern_fast,
                      "flops_per_bin_iter": fast_flops_per_bin_iter(M),
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "conventional": {"value": conv_value, "unit": UNIT, "ms_per_step": statistics.mean(ms_conv),

@@ -413,7 +413,7 @@ static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
 
 template <int M, int ST>
 static cudaError_t launch_conv_m(const ConvEmArgs& a, cudaStream_t st) {
-  return em_threads(M, a.N) == 128 ? launch_conv_t<M, ST, 128>(a, st) : launch_conv_t<M, ST, 256>(a, st);
+  return launch_conv_t<M, ST, 128>(a, st);
 }
 
 template <int ST>

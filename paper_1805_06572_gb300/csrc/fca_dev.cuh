@@ -195,9 +195,11 @@ __device__ __forceinline__ float warp_sum(float x) {
 // called by all 32 lanes of one warp and ends with __syncwarp().
 struct WarpLA {
   float2 A[kMaxM][kMaxM];   // work matrix (eigenproblem)
-  float2 L[kMaxM][kMaxM];   // Cholesky factor (lower triangle)
+  float2 L[kMaxM][kMaxM];   // Cholesky factor (lower triangle); L^-1 in the fast solver
   float2 Z[kMaxM][kMaxM];   // temporary
   float2 V[kMaxM][kMaxM];   // eigenvectors / result
+  float2 A2[kMaxM][kMaxM];  // ping-pong partners of A and V (fast solver)
+  float2 V2[kMaxM][kMaxM];
   float invd[kMaxM];        // 1 / L_ii
   float2 jself[kMaxM + 1];  // Jacobi: J_xx for every index x
   float2 joth[kMaxM + 1];   // Jacobi: J_{partner(x), x}
@@ -433,6 +435,289 @@ __device__ int warp_gevd(WarpLA& la, int lane, float* sig, double* logdetQ) {
     if (!(s > 0.f) || !(s < 3.0e38f)) return kErrNotPD;
   }
   return kOk;
+}
+
+// ---------------------------------------------------------------- low-latency solver
+// The same generalised eigenproblem as warp_gevd, arranged for a short dependency chain:
+// one lane factors B = L L^H and inverts L in registers (no warp synchronisation inside the
+// recurrences), the congruence W = L^-1 A L^-H and Q = L^-H U are lane-parallel products,
+// and the Jacobi rounds ping-pong between two copies of A and V (one __syncwarp fewer per
+// round).
+
+// Lane 0: B (lower triangle of la.L) = L L^H; writes L^-1 (lower, zero above) over la.L and
+// returns log|det L^-H|^2 = 2 sum_i log(1/L_ii). Result is valid on lane 0 only; *ok too.
+template <int M>
+__device__ float lane_cholesky_inverse(WarpLA& la, bool* ok) {
+  float2 L[M][M];
+  float id[M];
+  bool good = true;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+#pragma unroll
+    for (int i = j; i < M; ++i) {
+      float2 s = la.L[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = csub(s, cmulc(L[i][k], L[j][k]));
+      if (i == j) {
+        const float piv = s.x;
+        good = good && (piv > 0.f) && (piv < 3.0e38f);
+        float il = rsqrtf(piv);
+        il = il * fmaf(-0.5f * piv * il, il, 1.5f);  // Newton step: 1/sqrt to rounding
+        id[j] = il;
+        L[j][j] = make_float2(piv * il, 0.f);
+      } else {
+        L[i][j] = cscale(s, id[j]);
+      }
+    }
+  }
+  // L^-1: (L^-1)_ii = id_i; (L^-1)_ij = -id_i sum_{k=j}^{i-1} L_ik (L^-1)_kj for i > j.
+  float2 Li[M][M];
+  float ld = 0.f;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    Li[j][j] = make_float2(id[j], 0.f);
+    ld += 2.f * logf(id[j]);
+#pragma unroll
+    for (int i = j + 1; i < M; ++i) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = j; k < i; ++k) s = cfma(L[i][k], Li[k][j], s);
+      Li[i][j] = cscale(s, -id[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    la.invd[i] = id[i];
+#pragma unroll
+    for (int j = 0; j < M; ++j) la.L[i][j] = (j <= i) ? Li[i][j] : make_float2(0.f, 0.f);
+  }
+  *ok = good;
+  return ld;
+}
+
+// la.A <- W = Li A Li^H (Li = la.L, lower triangular), Hermitian by construction.
+template <int M>
+__device__ void warp_congruence_products(WarpLA& la, int lane) {
+  constexpr int kPer = (M * M + 31) / 32;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {  // Z = A Li^H:  Z_ij = sum_{k<=j} A_ik conj(Li_jk)
+    const int e = lane + 32 * t;
+    if (e < M * M) {
+      const int i = e / M, j = e % M;
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k <= j) s = cadd(s, cmulc(la.A[i][k], la.L[j][k]));
+      la.Z[i][j] = s;
+    }
+  }
+  __syncwarp();
+  constexpr int NU = M * (M + 1) / 2;  // upper triangle incl. diagonal
+  constexpr int kPerU = (NU + 31) / 32;
+#pragma unroll
+  for (int t = 0; t < kPerU; ++t) {  // W_ij = sum_{k<=i} Li_ik Z_kj, i <= j
+    const int u = lane + 32 * t;
+    if (u < NU) {
+      int i = 0, r = u;
+      while (r >= M - i) {
+        r -= M - i;
+        ++i;
+      }
+      const int j = i + r;
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k <= i) s = cfma(la.L[i][k], la.Z[k][j], s);
+      if (i == j) {
+        la.A[i][i] = make_float2(s.x, 0.f);
+      } else {
+        la.A[i][j] = s;
+        la.A[j][i] = cconj(s);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Jacobi as warp_jacobi, reading A/V from one buffer and writing the other each round.
+// On return the current buffers are la.A / la.V (an even number of swaps is enforced by
+// a final copy when needed).
+template <int M>
+__device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
+  constexpr int n = M + (M & 1);
+  constexpr int kPer = (M * M + 31) / 32;
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e - (e / M) * M;
+    la.V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncwarp();
+  if (M == 1) return 0;
+  const float tol2 = tol * tol;
+  float2(*Ac)[kMaxM] = la.A;
+  float2(*Vc)[kMaxM] = la.V;
+  float2(*An)[kMaxM] = la.A2;
+  float2(*Vn)[kMaxM] = la.V2;
+  int result = -1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rotated = 0, big = 0;
+    for (int r = 0; r < n - 1; ++r) {
+      if (lane < n / 2) {
+        const int k = lane;
+        const int a = (k == 0) ? r : (r + k) % (n - 1);
+        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
+        const int p = min(a, b), q = max(a, b);
+        float c = 1.f, s = 0.f;
+        float2 e = make_float2(1.f, 0.f);
+        if (q < M) {
+          const float app = Ac[p][p].x, aqq = Ac[q][q].x;
+          const float2 apq = Ac[p][q];
+          const float r2 = cabs2(apq);
+          const float den = fabsf(app * aqq);
+          if (r2 > tol2 * den && r2 > 1e-36f) {
+            big |= (r2 > 1e-8f * den);
+            float ir = rsqrtf(r2);
+            ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);   // 1 / |a_pq|, Newton-refined
+            const float tau = 0.5f * (aqq - app) * ir;
+            const float h = fmaf(tau, tau, 1.f);
+            const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
+            const float g = fmaf(t, t, 1.f);
+            c = rsqrtf(g);
+            c = c * fmaf(-0.5f * g * c, c, 1.5f);         // Newton-refined: c^2 + s^2 = 1
+            s = t * c;
+            e = cscale(apq, ir);
+            rotated = 1;
+          }
+          la.jself[p] = make_float2(c, 0.f);
+          la.joth[p] = cscale(cconj(e), -s);
+          la.partner[p] = q;
+          la.jself[q] = cscale(cconj(e), c);
+          la.joth[q] = make_float2(s, 0.f);
+          la.partner[q] = p;
+        } else {
+          la.jself[p] = make_float2(1.f, 0.f);
+          la.joth[p] = make_float2(0.f, 0.f);
+          la.partner[p] = p;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = lane + 32 * t;
+        if (e < M * M) {
+          const int i = e / M, l = e - (e / M) * M;
+          const int ip = la.partner[i], lp = la.partner[l];
+          const float2 Ji = la.jself[i], Jo_i = la.joth[i], Jl = la.jself[l], Jo_l = la.joth[l];
+          const float2 r0 = cfma(Ac[i][lp], Jo_l, cmul(Ac[i][l], Jl));
+          const float2 r1 = cfma(Ac[ip][lp], Jo_l, cmul(Ac[ip][l], Jl));
+          float2 v = cadd(ccmul(Ji, r0), ccmul(Jo_i, r1));
+          if (i == l) v.y = 0.f;
+          else if (ip == l) v = make_float2(0.f, 0.f);  // the pivot pair
+          An[i][l] = v;
+          Vn[i][l] = cfma(Vc[i][lp], Jo_l, cmul(Vc[i][l], Jl));
+        }
+      }
+      __syncwarp();
+      float2(*t0)[kMaxM] = Ac;
+      Ac = An;
+      An = t0;
+      t0 = Vc;
+      Vc = Vn;
+      Vn = t0;
+    }
+    if (!__any_sync(0xffffffffu, rotated) || !__any_sync(0xffffffffu, big)) {
+      result = sweep + 1;
+      break;
+    }
+  }
+  if (Ac != la.A) {  // bring the result back to la.A / la.V
+    for (int e = lane; e < M * M; e += 32) {
+      const int i = e / M, j = e % M;
+      la.A[i][j] = Ac[i][j];
+      la.V[i][j] = Vc[i][j];
+    }
+    __syncwarp();
+  }
+  return result;
+}
+
+// Low-latency generalised eigenproblem of (A, B) in (la.A, la.L): writes Q = L^-H U into
+// Qout and U into Uout ([kMaxM][kMaxM]), Sig into sig, and returns 2 sum_i log(1/L_ii) in
+// *ldL. log|det Q|^2 = *ldL + log|det U|^2, where the FP32 rotations leave U unitary only to
+// rounding: log|det U|^2 = ||U||_F^2 - M to first order, which the caller sums in FP64 from
+// Uout (unitarity_defect). Returns a device status code.
+template <int M>
+__device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[kMaxM],
+                              float2 (*Uout)[kMaxM], float* ldL) {
+  bool ok = true;
+  float ld = 0.f;
+  if (lane == 0) ld = lane_cholesky_inverse<M>(la, &ok);
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  __syncwarp();
+  if (!ok) return kErrNotPD;
+  warp_congruence_products<M>(la, lane);
+  const int sw = warp_jacobi_pp<M>(la, lane, 2.0e-7f, 30);
+  if (sw < 0) return kErrEigNoConv;
+  if (lane < M) sig[lane] = la.A[lane][lane].x;
+  constexpr int kPer = (M * M + 31) / 32;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {  // Q_ij = sum_{k>=i} conj(Li_ki) U_kj
+    const int e = lane + 32 * t;
+    if (e < M * M) {
+      const int i = e / M, j = e % M;
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k >= i) s = cadd(s, ccmul(la.L[k][i], la.V[k][j]));
+      Qout[i][j] = s;
+      Uout[i][j] = la.V[i][j];
+    }
+  }
+  ld = __shfl_sync(0xffffffffu, ld, 0);
+  __syncwarp();
+  *ldL = ld;
+  for (int i = 0; i < M; ++i) {
+    const float sv = sig[i];
+    if (!(sv > 0.f) || !(sv < 3.0e38f)) return kErrNotPD;
+  }
+  return kOk;
+}
+
+// ||U||_F^2 - M in FP64 (all lanes get the result).
+template <int M>
+__device__ double unitarity_defect(const float2 (*U)[kMaxM], int lane) {
+  double un = 0.0;
+  for (int e = lane; e < M * M; e += 32) {
+    const float2 u = U[e / M][e % M];
+    un = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, un));
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
+  return un - (double)M;
+}
+
+// P <- P Q in FP64 (Eq. (updatePeff)) with Q given explicitly (FP32).
+template <int M>
+__device__ void warp_update_basis_q(double2 (*P)[kMaxM], const float2 (*Q)[kMaxM], int lane) {
+  constexpr int kPer = (M * M + 31) / 32;
+  double2 out[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = lane + 32 * t;
+    if (e < M * M) {
+      const int i = e / M, c = e - (e / M) * M;
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int m = 0; m < M; ++m) s = zfma(P[i][m], c2z(Q[m][c]), s);
+      out[t] = s;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = lane + 32 * t;
+    if (e < M * M) P[e / M][e % M] = out[t];
+  }
+  __syncwarp();
 }
 
 // P <- P Q in FP64 (Eq. (updatePeff)); P in shared memory [M][M] double2, Q = la.V (FP32).

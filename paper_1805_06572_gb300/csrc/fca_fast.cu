@@ -13,14 +13,14 @@
 //     log-likelihood terms log d_i + |yt_i|^2 / d_i     Eq. (like) in the transformed basis
 //   CTA reduction: per-lane FP32 partials -> warp transpose-reduction (FP32) -> cross-warp
 //     merge in FP64, in a fixed order (bitwise reproducible);
-//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8), P <- P Q in FP64
-//     (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)),
-//     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use).
+//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8) and the next
+//     basis P^H for the bin pass; meanwhile warp 1 does the previous iteration's FP64
+//     bookkeeping: P <- P Q (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)),
+//     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use), and the
+//     previous iteration's log-likelihood.
 // The log-likelihood of iteration l uses log det Rx = sum_i log d_i + log det S2 and
 // y^H Rx^-1 y = sum_i |yt_i|^2 / d_i, which follow from Rx = P^-H (v1 Lam + v2 I) P^-1.
-// The mixture and v stay in shared memory across iterations when they fit. The FP64
-// bookkeeping of an iteration (basis product, log-determinant, log-likelihood) runs in
-// warp 0 after the next basis has been published, overlapping the next bin pass.
+// The mixture and v stay in shared memory across iterations when they fit.
 #include "fca_dev.cuh"
 #include "fca_internal.h"
 
@@ -30,16 +30,19 @@ template <int M, int NW>
 struct FastShared {
   static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
   float red[NW][V];
-  float tot32[V];      // merged sums / N (Gram entries) for the eigensolver
-  double tot[V];       // merged sums in FP64
-  double2 P[kMaxM][kMaxM];  // basis P (FP64)
-  float2 P32[kMaxM][kMaxM]; // P rounded to FP32
-  float2 PH[M][M];     // FP32 P^H (times the decode scale) used by the bin pass
+  double2 P[kMaxM][kMaxM];      // basis P (FP64)
+  float2 P32[kMaxM][kMaxM];     // P rounded to FP32
+  float2 PH[M][M];              // FP32 P^H (times the decode scale) used by the bin pass
   float lam[M], ilam[M];
   double lam64[kMaxM];
-  float sig[kMaxM];
+  // Double-buffered results of an iteration's eigensolve, consumed by the deferred FP64
+  // bookkeeping one iteration later.
+  float2 Q[2][kMaxM][kMaxM];
+  float2 U[2][kMaxM][kMaxM];
+  float sig[2][kMaxM];
+  float ldL[2];                 // 2 sum log(1/L_ii): log|det Q|^2 = ldL + log|det U|^2
+  double llt[2][2];             // sum log d, sum p/d of the iteration
   double logdetS2;
-  double ldQ;
   int fail;          // read by every thread after a barrier; written only before one
   int fail_pending;  // set by the deferred bookkeeping, folded into `fail` by warp 0
   WarpLA la;
@@ -53,13 +56,44 @@ __host__ __device__ constexpr int pair_index(int M, int i, int k) {  // i < k
 // CTAs per SM hide each CTA's serial per-bin eigensolver behind the others' bin passes).
 __host__ __device__ constexpr int fast_min_blocks(int M) { return M <= 4 ? 4 : (M <= 6 ? 3 : 2); }
 
+// Deferred FP64 bookkeeping of iteration `it` (one warp): P <- P Q (Eq. (updatePeff)),
+// Lambda <- Sigma (Eq. (updateLambdaeff)), the log-likelihood of iteration it (at its own
+// parameters), log det S2 of the next iteration, and the parameters of iteration L-1.
+template <int M, typename Sh>
+__device__ void fast_deferred(Sh& sh, const FastEmArgs& a, int f, int it, int lane) {
+  constexpr int MM = M * M;
+  const int b = it & 1;
+  warp_update_basis_q<M>(sh.P, sh.Q[b], lane);
+  for (int e = lane; e < MM; e += 32) sh.P32[e / M][e % M] = z2c(sh.P[e / M][e % M]);
+  if (lane < M) sh.lam64[lane] = (double)sh.sig[b][lane];
+  if (lane == 0) {
+    const double ll = -(double)a.N * M * 1.1447298858494002 - sh.llt[b][0] - sh.llt[b][1] -
+                      (double)a.N * sh.logdetS2;
+    a.llf[(size_t)it * a.F + f] = ll;
+    if (!isfinite(ll)) {
+      set_status(a.status, kErrNonFinite);
+      sh.fail_pending = kErrNonFinite;
+    }
+  }
+  // log det S2 = -log|det P|^2 and P <- P Q: subtract log|det Q|^2 of the Q applied.
+  const double ldQ = (double)sh.ldL[b] + unitarity_defect<M>(sh.U[b], lane);
+  if (lane == 0) sh.logdetS2 -= ldQ;
+  __syncwarp();
+  if (it == a.iters - 2) {  // the parameters of iteration L-1
+    for (int e = lane; e < MM; e += 32) a.P_prev[(size_t)f * MM + e] = sh.P[e / M][e % M];
+    if (lane < M) a.lam_prev[(size_t)f * M + lane] = sh.lam64[lane];
+    if (lane == 0) a.logdetS2_prev[f] = sh.logdetS2;
+  }
+  __syncwarp();
+}
+
 template <int M, int ST, int NT>
 __global__ void __launch_bounds__(NT, fast_min_blocks(M)) fast_em_kernel(const FastEmArgs a) {
   using E = typename Elem<ST>::T;
   constexpr int NW = NT / 32;
+  static_assert(NW >= 2, "the deferred bookkeeping runs on warp 1");
   using Sh = FastShared<M, NW>;
   constexpr int V = Sh::V;
-  using RS = RedShape<V>;
   constexpr int MM = M * M;
   constexpr bool kHoist = (M <= 4);
   __shared__ Sh sh;
@@ -127,8 +161,11 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M)) fast_em_kernel(const F
   }
   __syncthreads();
 
+  int done = 0;  // iterations whose bin pass and eigensolve completed
   for (int it = 0; it < a.iters; ++it) {
     const bool last = (it == a.iters - 1);
+    const int b = it & 1;
+    using RS = RedShape<V>;
     float acc[RS::NA];
 #pragma unroll
     for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
@@ -222,88 +259,81 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M)) fast_em_kernel(const F
 
     warp_reduce_store<V>(acc, lane, sh.red[warp]);
     __syncthreads();
-    for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps (pairwise)
-      double s[NW];
+    // Fixed-order FP64 merge across warps (pairwise), written straight into the FP32
+    // matrices St_j = sums / N of the eigensolver (Hermitian) and the two LL sums.
+    for (int e = tid; e < MM + 2; e += NT) {
+      if (e < MM) {
+        const int i = e / M, j = e % M;
+        const int lo = min(i, j), hi = max(i, j);
+        const int o = (i == j) ? i : M + 2 * pair_index(M, lo, hi);
+        double s1r[NW], s1i[NW], s2r[NW], s2i[NW];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s[w] = (double)sh.red[w][i];
+        for (int w = 0; w < NW; ++w) {
+          s1r[w] = (double)sh.red[w][o];
+          s2r[w] = (double)sh.red[w][MM + o];
+          s1i[w] = (i == j) ? 0.0 : (double)sh.red[w][o + 1];
+          s2i[w] = (i == j) ? 0.0 : (double)sh.red[w][MM + o + 1];
+        }
 #pragma unroll
-      for (int h = NW / 2; h >= 1; h >>= 1)
+        for (int h = NW / 2; h >= 1; h >>= 1)
 #pragma unroll
-        for (int w = 0; w < h; ++w) s[w] += s[w + h];
-      sh.tot[i] = s[0];
-      sh.tot32[i] = (float)(s[0] * invN);
+          for (int w = 0; w < h; ++w) {
+            s1r[w] += s1r[w + h];
+            s1i[w] += s1i[w + h];
+            s2r[w] += s2r[w + h];
+            s2i[w] += s2i[w + h];
+          }
+        const float sg = (i <= j) ? 1.f : -1.f;
+        sh.la.A[i][j] = make_float2((float)(s1r[0] * invN), sg * (float)(s1i[0] * invN));
+        sh.la.L[i][j] = make_float2((float)(s2r[0] * invN), sg * (float)(s2i[0] * invN));
+      } else {
+        const int o = 2 * MM + (e - MM);
+        double sv[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sv[w] = (double)sh.red[w][o];
+#pragma unroll
+        for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+          for (int w = 0; w < h; ++w) sv[w] += sv[w + h];
+        sh.llt[b][e - MM] = sv[0];
+      }
     }
     __syncthreads();
 
     if (warp == 0) {
-      if (lane == 0 && sh.fail_pending) sh.fail = sh.fail_pending;
-      for (int e = lane; e < MM; e += 32) {  // St_j = sums / N, Hermitian, FP32
-        const int i = e / M, j = e % M;
-        float2 s1v, s2v;
-        if (i == j) {
-          s1v = make_float2(sh.tot32[i], 0.f);
-          s2v = make_float2(sh.tot32[MM + i], 0.f);
-        } else {
-          const int lo = min(i, j), hi = max(i, j);
-          const int o = M + 2 * pair_index(M, lo, hi);
-          const float sg = (i < j) ? 1.f : -1.f;
-          s1v = make_float2(sh.tot32[o], sg * sh.tot32[o + 1]);
-          s2v = make_float2(sh.tot32[MM + o], sg * sh.tot32[MM + o + 1]);
-        }
-        sh.la.A[i][j] = s1v;
-        sh.la.L[i][j] = s2v;
+      float ldL = 0.f;
+      const int rc = warp_gevd_fast<M>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL);
+      if (lane == 0) sh.ldL[b] = ldL;
+      if (rc != kOk && lane == 0) {
+        set_status(a.status, rc);
+        sh.fail = rc;
       }
-      __syncwarp();
-      double ldQ = 0.0;
-      const int rc = warp_gevd<M>(sh.la, lane, sh.sig, &ldQ);
-      if (rc != kOk) {
-        if (lane == 0) {
-          set_status(a.status, rc);
-          sh.fail = rc;
-        }
-      } else {
+    } else if (warp == 1 && it > 0) {
+      fast_deferred<M>(sh, a, f, it - 1, lane);
+    }
+    if (warp < 2) asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (warp == 0) {
+      if (lane == 0 && sh.fail_pending) sh.fail = sh.fail_pending;
+      if (!sh.fail) {
         // Publish the next basis for the bin pass: P^H <- (P Q)^H from the FP32 copies.
         for (int e = lane; e < MM; e += 32) {
           const int i = e / M, m = e % M;  // (P Q)_{m i}
           float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.la.V[k][i], s);
+          for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
           sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
         }
         if (lane < M) {
-          sh.lam[lane] = sh.sig[lane];
-          sh.ilam[lane] = 1.f / sh.sig[lane];
+          sh.lam[lane] = sh.sig[b][lane];
+          sh.ilam[lane] = 1.f / sh.sig[b][lane];
         }
-        if (lane == 0) sh.ldQ = ldQ;
       }
     }
     __syncthreads();
     if (sh.fail) break;
-    if (warp == 0) {
-      // Deferred FP64 bookkeeping (overlaps the other warps' next bin pass): P <- P Q
-      // (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)), the log-likelihood of
-      // this iteration, log det S2 of the next one.
-      warp_update_basis<M>(sh.P, sh.la, lane);
-      for (int e = lane; e < MM; e += 32) sh.P32[e / M][e % M] = z2c(sh.P[e / M][e % M]);
-      if (lane < M) sh.lam64[lane] = (double)sh.sig[lane];
-      if (lane == 0) {
-        const double ll = -(double)N * M * 1.1447298858494002 - sh.tot[2 * MM] -
-                          sh.tot[2 * MM + 1] - (double)N * sh.logdetS2;
-        a.llf[(size_t)it * F + f] = ll;
-        if (!isfinite(ll)) {
-          set_status(a.status, kErrNonFinite);
-          sh.fail_pending = kErrNonFinite;
-        }
-        sh.logdetS2 -= sh.ldQ;  // log det S2 = -log|det P|^2, P <- P Q
-      }
-      __syncwarp();
-      if (it == a.iters - 2) {  // the parameters of iteration L-1
-        for (int e = lane; e < MM; e += 32) a.P_prev[(size_t)f * MM + e] = sh.P[e / M][e % M];
-        if (lane < M) a.lam_prev[(size_t)f * M + lane] = sh.lam64[lane];
-        if (lane == 0) a.logdetS2_prev[f] = sh.logdetS2;
-      }
-    }
+    done = it + 1;
   }
+  if (warp == 1 && done > 0 && done == a.iters) fast_deferred<M>(sh, a, f, done - 1, lane);
   __syncthreads();
 
   if (tid < MM) a.P[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
@@ -387,7 +417,7 @@ static cudaError_t launch_fast_t(const FastEmArgs& a0, cudaStream_t st) {
 
 template <int M, int ST>
 static cudaError_t launch_fast_m(const FastEmArgs& a, cudaStream_t st) {
-  return em_threads(M, a.N) == 128 ? launch_fast_t<M, ST, 128>(a, st) : launch_fast_t<M, ST, 256>(a, st);
+  return launch_fast_t<M, ST, 128>(a, st);
 }
 
 template <int ST>
