@@ -129,6 +129,13 @@ struct LogProd {
   }
   // Call at most every 8 factors (m < 2^8) to keep m in range.
   __device__ __forceinline__ float log() const { return logf(m) + 0.6931471805599453f * (float)e; }
+  // Same value with the mantissa product renormalised to [1, 2), where the hardware log2
+  // approximation has an absolute error of at most 2^-22.
+  __device__ __forceinline__ float log_fast() const {
+    const int b = __float_as_int(m);
+    const float mm = __int_as_float((b & 0x007fffff) | 0x3f800000);
+    return 0.6931471805599453f * (__log2f(mm) + (float)(e + (b >> 23) - 127));
+  }
 };
 
 // ------------------------------------------------------------ warp transpose reduction

@@ -206,54 +206,58 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M)) fast_em_kernel(const F
         }
         yt[i] = s;
       }
-      float ca[M], cb[M], cc[M];
-      float s1 = 0.f, s2 = 0.f, ql = 0.f;
+      // With r_i = 1/d_i, t_i = lam_i r_i and q_i = |yt_i|^2 r_i^2 (d_i = v1 lam_i + v2):
+      //   v1' = (v1/M)(v1 sum lam_i q_i + v2 sum r_i)     (Eq. (updateveff), j = 1)
+      //   v2' = (v2/M)(v2 sum q_i + v1 sum t_i)           (Eq. (updateveff), j = 2)
+      //   mut1_i / sqrt(v1') = (v1 / sqrt(v1')) t_i yt_i, mut2_i / sqrt(v2') = (v2 / sqrt(v2')) r_i yt_i
+      //   c_i / v_j' = (v1 v2 / v_j') t_i                 (Eq. (updatePhitildeeff))
+      float r[M], t[M], pp[M];
+      float sA = 0.f, sB = 0.f, sC = 0.f, sD = 0.f, ql = 0.f;
       LogProd lp;
-      const float v12 = v1 * v2;
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        const float e = v1 * lamr[i];
-        const float d = e + v2;
-        const float r = __fdividef(1.f, d);
-        const float p = cabs2(yt[i]);
-        ca[i] = e * r;        // mut1_i = ca_i yt_i
-        cb[i] = v2 * r;       // mut2_i = cb_i yt_i
-        cc[i] = v2 * ca[i];   // v1 v2 lam_i / d_i
-        s1 = fmaf(ca[i] * ca[i] * p, ilamr[i], fmaf(v12, r, s1));  // (|mut1|^2 + c) / lam
-        s2 = fmaf(cb[i] * cb[i], p, s2 + cc[i]);                   // |mut2|^2 + c
-        ql = fmaf(p, r, ql);
+        const float d = fmaf(v1, lamr[i], v2);
+        r[i] = __fdividef(1.f, d);
+        pp[i] = cabs2(yt[i]);
+        t[i] = lamr[i] * r[i];
+        const float pr = pp[i] * r[i];
+        const float q = pr * r[i];
+        sA = fmaf(lamr[i], q, sA);
+        sB += r[i];
+        sC += q;
+        sD += t[i];
+        ql += pr;
         lp.mul(d);
       }
-      const float v1n = fmaxf(s1 * (1.f / M), vf);
-      const float v2n = fmaxf(s2 * (1.f / M), vf);
+      const float v1n = fmaxf((v1 * (1.f / M)) * fmaf(v1, sA, v2 * sB), vf);
+      const float v2n = fmaxf((v2 * (1.f / M)) * fmaf(v2, sC, v1 * sD), vf);
       v1p[n] = v1n;
       v2p[n] = v2n;
-      const float r1 = rsqrtf(v1n), r2 = rsqrtf(v2n);
-      const float w1 = r1 * r1, w2 = r2 * r2;
-      float2 u[M], t[M];  // mut_j / sqrt(v_j')
+      const float rs1 = rsqrtf(v1n), rs2 = rsqrtf(v2n);
+      const float a1 = v1 * rs1, a2 = v2 * rs2;
+      const float v12 = v1 * v2;
+      const float k1 = v12 * (rs1 * rs1), k2 = v12 * (rs2 * rs2);
+      float s1[M], s2[M];
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        u[i] = cscale(yt[i], ca[i] * r1);
-        t[i] = cscale(yt[i], cb[i] * r2);
-      }
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        acc[i] += fmaf(cc[i], w1, cabs2(u[i]));
-        acc[MM + i] += fmaf(cc[i], w2, cabs2(t[i]));
+        s1[i] = a1 * t[i];
+        s2[i] = a2 * r[i];
+        acc[i] = fmaf(s1[i] * s1[i], pp[i], fmaf(k1, t[i], acc[i]));
+        acc[MM + i] = fmaf(s2[i] * s2[i], pp[i], fmaf(k2, t[i], acc[MM + i]));
       }
 #pragma unroll
       for (int i = 0; i < M; ++i)
 #pragma unroll
         for (int k = i + 1; k < M; ++k) {
           const int o = M + 2 * pair_index(M, i, k);
-          const float2 zu = cmulc(u[i], u[k]);
-          const float2 zt = cmulc(t[i], t[k]);
-          acc[o] += zu.x;
-          acc[o + 1] += zu.y;
-          acc[MM + o] += zt.x;
-          acc[MM + o + 1] += zt.y;
+          const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
+          const float w1 = s1[i] * s1[k], w2 = s2[i] * s2[k];
+          acc[o] = fmaf(w1, z.x, acc[o]);
+          acc[o + 1] = fmaf(w1, z.y, acc[o + 1]);
+          acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
+          acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
         }
-      acc[2 * MM] += lp.log();
+      acc[2 * MM] += lp.log_fast();
       acc[2 * MM + 1] += ql;
     }
 
