@@ -689,6 +689,160 @@ __device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[k
   return kOk;
 }
 
+// Single-lane version of warp_gevd_fast for small M: the whole generalised eigenproblem in
+// one thread's registers (Cholesky and its inverse, the congruence, a cyclic Jacobi on the
+// upper triangle, Q = L^-H U), with no warp synchronisation or shared-memory round trips.
+// At M <= 4 a parallel Jacobi round costs more in synchronisation than its rotations.
+// Inputs A, B (Hermitian, B positive definite) are read from shared memory; outputs as
+// warp_gevd_fast. Returns a device status code.
+template <int M>
+__device__ int lane_gevd(const float2 (*A)[kMaxM], const float2 (*B)[kMaxM], float* sig,
+                         float2 (*Qout)[kMaxM], float2 (*Uout)[kMaxM], float* ldL, float tol,
+                         int max_sweeps) {
+  // Cholesky B = L L^H and L^-1.
+  float2 L[M][M];
+  float id[M];
+  bool good = true;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+#pragma unroll
+    for (int i = j; i < M; ++i) {
+      float2 sv = B[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) sv = csub(sv, cmulc(L[i][k], L[j][k]));
+      if (i == j) {
+        const float piv = sv.x;
+        good = good && (piv > 0.f) && (piv < 3.0e38f);
+        float il = rsqrtf(piv);
+        il = il * fmaf(-0.5f * piv * il, il, 1.5f);
+        id[j] = il;
+        L[j][j] = make_float2(piv * il, 0.f);
+      } else {
+        L[i][j] = cscale(sv, id[j]);
+      }
+    }
+  }
+  if (!good) return kErrNotPD;
+  float2 Li[M][M];
+  float ld = 0.f;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    Li[j][j] = make_float2(id[j], 0.f);
+    ld += 2.f * logf(id[j]);
+#pragma unroll
+    for (int i = j + 1; i < M; ++i) {
+      float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = j; k < i; ++k) sv = cfma(L[i][k], Li[k][j], sv);
+      Li[i][j] = cscale(sv, -id[i]);
+    }
+  }
+  // W = Li A Li^H: T = A Li^H, then the upper triangle of Li T.
+  float2 T[M][M];
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k <= j; ++k) sv = cadd(sv, cmulc(A[i][k], Li[j][k]));
+      T[i][j] = sv;
+    }
+  float2 W[M][M];  // only i <= j is kept up to date
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = i; j < M; ++j) {
+      float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k <= i; ++k) sv = cfma(Li[i][k], T[k][j], sv);
+      W[i][j] = (i == j) ? make_float2(sv.x, 0.f) : sv;
+    }
+  float2 V[M][M];
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < M; ++j) V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  // Cyclic Jacobi (row order), rotation as in warp_jacobi: J_pp = c, J_pq = s,
+  // J_qp = -s conj(e), J_qq = c conj(e); rows p, q of W change by J^H, columns of V by J.
+  const float tol2 = tol * tol;
+  int sweeps = -1;
+  if (M == 1) sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
+    bool rotated = false, big = false;
+#pragma unroll
+    for (int p = 0; p < M - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < M; ++q) {
+        const float app = W[p][p].x, aqq = W[q][q].x;
+        const float2 apq = W[p][q];
+        const float r2 = cabs2(apq);
+        const float den = fabsf(app * aqq);
+        if (r2 > tol2 * den && r2 > 1e-36f) {
+          rotated = true;
+          big = big || (r2 > 1e-8f * den);
+          float ir = rsqrtf(r2);
+          ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
+          const float tau = 0.5f * (aqq - app) * ir;
+          const float h = fmaf(tau, tau, 1.f);
+          const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
+          const float g = fmaf(t, t, 1.f);
+          float c = rsqrtf(g);
+          c = c * fmaf(-0.5f * g * c, c, 1.5f);
+          const float sn = t * c;
+          const float2 e = cscale(apq, ir);
+          const float2 mse = cscale(e, -sn);          // -s e
+          const float2 cec = cscale(cconj(e), c);     // c conj(e)
+          const float2 msec = cscale(cconj(e), -sn);  // -s conj(e)
+          // Off-block entries (p,k), (q,k): x' = c x - s e y, y' = s x + c conj(e)^* ... (J^H rows)
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            if (k == p || k == q) continue;
+            const float2 x = (p < k) ? W[p][k] : cconj(W[k][p]);
+            const float2 y = (q < k) ? W[q][k] : cconj(W[k][q]);
+            const float2 xn = cfma(mse, y, cscale(x, c));
+            const float2 yn = cfma(cconj(cec), y, cscale(x, sn));
+            if (p < k) W[p][k] = xn; else W[k][p] = cconj(xn);
+            if (q < k) W[q][k] = yn; else W[k][q] = cconj(yn);
+          }
+          const float rr = r2 * ir;  // |a_pq|
+          W[p][p] = make_float2(app - t * rr, 0.f);
+          W[q][q] = make_float2(aqq + t * rr, 0.f);
+          W[p][q] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < M; ++k) {  // V <- V J
+            const float2 vp = V[k][p], vq = V[k][q];
+            V[k][p] = cfma(vq, msec, cscale(vp, c));
+            V[k][q] = cfma(vq, cec, cscale(vp, sn));
+          }
+        }
+      }
+    if (!rotated || !big) {
+      sweeps = sweep + 1;
+      break;
+    }
+  }
+  if (sweeps < 0) return kErrEigNoConv;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    sig[i] = W[i][i].x;
+    if (!(W[i][i].x > 0.f) || !(W[i][i].x < 3.0e38f)) good = false;
+  }
+  // Q = Li^H V: Q_ij = sum_{k>=i} conj(Li_ki) V_kj.
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = i; k < M; ++k) sv = cadd(sv, ccmul(Li[k][i], V[k][j]));
+      Qout[i][j] = sv;
+      Uout[i][j] = V[i][j];
+    }
+  *ldL = ld;
+  return good ? kOk : kErrNotPD;
+}
+
 // ||U||_F^2 - M in FP64 (all lanes get the result).
 template <int M>
 __device__ double unitarity_defect(const float2 (*U)[kMaxM], int lane) {

@@ -56,6 +56,29 @@ __host__ __device__ constexpr int pair_index(int M, int i, int k) {  // i < k
 // CTAs per SM hide each CTA's serial per-bin eigensolver behind the others' bin passes).
 __host__ __device__ constexpr int fast_min_blocks(int M) { return M <= 4 ? 4 : (M <= 6 ? 3 : 2); }
 
+// Value v of the per-warp partial-sum vector -> the Hermitian matrix entry it belongs to:
+// Gram g (0, 1), row i, column k (i <= k), and part (0 = real, 1 = imaginary).
+template <int M>
+__device__ __forceinline__ void value_entry(int v, int* g, int* i, int* k, int* part) {
+  constexpr int MM = M * M;
+  *g = v / MM;
+  int r = v - *g * MM;
+  if (r < M) {
+    *i = *k = r;
+    *part = 0;
+    return;
+  }
+  r -= M;
+  *part = r & 1;
+  int pr = r >> 1, row = 0;
+  while (pr >= M - 1 - row) {
+    pr -= M - 1 - row;
+    ++row;
+  }
+  *i = row;
+  *k = row + 1 + pr;
+}
+
 // Deferred FP64 bookkeeping of iteration `it` (one warp): P <- P Q (Eq. (updatePeff)),
 // Lambda <- Sigma (Eq. (updateLambdaeff)), the log-likelihood of iteration it (at its own
 // parameters), log det S2 of the next iteration, and the parameters of iteration L-1.
@@ -263,50 +286,57 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M)) fast_em_kernel(const F
 
     warp_reduce_store<V>(acc, lane, sh.red[warp]);
     __syncthreads();
-    // Fixed-order FP64 merge across warps (pairwise), written straight into the FP32
-    // matrices St_j = sums / N of the eigensolver (Hermitian) and the two LL sums.
-    for (int e = tid; e < MM + 2; e += NT) {
-      if (e < MM) {
-        const int i = e / M, j = e % M;
-        const int lo = min(i, j), hi = max(i, j);
-        const int o = (i == j) ? i : M + 2 * pair_index(M, lo, hi);
-        double s1r[NW], s1i[NW], s2r[NW], s2i[NW];
+    // Merge the warp partials in a fixed order: Gram entries in FP32 (they feed the FP32
+    // eigensolver), the two log-likelihood sums with a compensated two-float sum kept in
+    // FP64. One value per thread.
+    for (int e = tid; e < V; e += NT) {
+      if (e < 2 * MM) {
+        float sv[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          s1r[w] = (double)sh.red[w][o];
-          s2r[w] = (double)sh.red[w][MM + o];
-          s1i[w] = (i == j) ? 0.0 : (double)sh.red[w][o + 1];
-          s2i[w] = (i == j) ? 0.0 : (double)sh.red[w][MM + o + 1];
-        }
-#pragma unroll
-        for (int h = NW / 2; h >= 1; h >>= 1)
-#pragma unroll
-          for (int w = 0; w < h; ++w) {
-            s1r[w] += s1r[w + h];
-            s1i[w] += s1i[w + h];
-            s2r[w] += s2r[w + h];
-            s2i[w] += s2i[w + h];
-          }
-        const float sg = (i <= j) ? 1.f : -1.f;
-        sh.la.A[i][j] = make_float2((float)(s1r[0] * invN), sg * (float)(s1i[0] * invN));
-        sh.la.L[i][j] = make_float2((float)(s2r[0] * invN), sg * (float)(s2i[0] * invN));
-      } else {
-        const int o = 2 * MM + (e - MM);
-        double sv[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) sv[w] = (double)sh.red[w][o];
+        for (int w = 0; w < NW; ++w) sv[w] = sh.red[w][e];
 #pragma unroll
         for (int h = NW / 2; h >= 1; h >>= 1)
 #pragma unroll
           for (int w = 0; w < h; ++w) sv[w] += sv[w + h];
-        sh.llt[b][e - MM] = sv[0];
+        const float val = sv[0] * (float)invN;
+        int g, i, k, part;
+        value_entry<M>(e, &g, &i, &k, &part);
+        float2(*D)[kMaxM] = g ? sh.la.L : sh.la.A;
+        if (i == k) {
+          D[i][i] = make_float2(val, 0.f);
+        } else if (part == 0) {
+          D[i][k].x = val;
+          D[k][i].x = val;
+        } else {
+          D[i][k].y = val;
+          D[k][i].y = -val;
+        }
+      } else {
+        float hi = sh.red[0][e], lo = 0.f;
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {  // TwoSum (Knuth): hi + lo = exact running sum
+          const float x = sh.red[w][e];
+          const float t = hi + x;
+          const float bp = t - hi;
+          lo += (hi - (t - bp)) + (x - bp);
+          hi = t;
+        }
+        sh.llt[b][e - 2 * MM] = (double)hi + (double)lo;
       }
     }
     __syncthreads();
 
     if (warp == 0) {
       float ldL = 0.f;
-      const int rc = warp_gevd_fast<M>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL);
+      int rc;
+      if constexpr (M <= 4) {
+        rc = kOk;
+        if (lane == 0) rc = lane_gevd<M>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL, 2.0e-7f, 30);
+        rc = __shfl_sync(0xffffffffu, rc, 0);
+        __syncwarp();
+      } else {
+        rc = warp_gevd_fast<M>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL);
+      }
       if (lane == 0) sh.ldL[b] = ldL;
       if (rc != kOk && lane == 0) {
         set_status(a.status, rc);
