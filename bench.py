@@ -214,6 +214,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pkg.build()
     from paper_1805_06572_gb300 import fca
+    from paper_1805_06572_gb300.shard import allreduce_max, weak_scaling_value
 
     dev = torch.device("cuda", local)
     c, mix, v0, S0 = synth.make_config(WORKLOAD, mixture_index=rank)
@@ -271,11 +272,7 @@ def main():
         return ms, kms, wall, launches
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return x if world == 1 else allreduce_max(x, dist, device=dev)
 
     for _ in range(args.warmup):
         step("fast")
@@ -303,9 +300,9 @@ def main():
     t_fast = max_over_ranks(sum(ms_fast) / 1e3)
     t_conv = max_over_ranks(sum(ms_conv) / 1e3)
     t_e2e = max_over_ranks(sum(ms_e2e) / 1e3)
-    value = world * units * args.steps / t_fast
-    conv_value = world * units * steps_conv / t_conv
-    e2e_value = world * units * args.steps / t_e2e
+    value = weak_scaling_value(units * args.steps, world, t_fast)
+    conv_value = weak_scaling_value(units * steps_conv, world, t_conv)
+    e2e_value = weak_scaling_value(units * args.steps, world, t_e2e)
     kern_fast = statistics.mean(k_fast) / 1e3
     kern_conv = statistics.mean(k_conv) / 1e3
     ach = fast_flops_per_bin_iter(M) * units / kern_fast / 1e12
