@@ -87,8 +87,9 @@ typedef struct {
  * state; on failure *out is NULL and nothing stays allocated. */
 fca_status fca_init(const fca_problem* p, void* cuda_stream, fca_state** out);
 
-/* Reload a state with a new mixture and initial parameters of the same M, F, N and storage.
- * Clears a failed status. The positivity floor of v is recomputed from the new y:
+/* Reload a state with a new mixture and initial parameters of the same M, F and storage and
+ * N frames, N at most the N the state was created with (its buffers are reused; later calls
+ * work on the new N). Clears a failed status. The positivity floor of v is recomputed from the new y:
  * vfloor(f) = max(1e-12 * mean_{n,m} |y_m(n,f)|^2, 1e-30) (applied after every v update). */
 fca_status fca_load(fca_state* s, const fca_problem* p, void* cuda_stream);
 
@@ -178,6 +179,84 @@ fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const void* y_de
                                const double* v0_dev, const double* S0_dev, int32_t iters,
                                float* v_dev, void* x1_dev, void* x2_dev, double* loglik_dev,
                                void* cuda_stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Batches: many mixtures, each with its own M, F and N, in one job.
+ *
+ * Every frequency bin of every mixture is an independent EM problem (all updates of Sec. 2
+ * and Sec. 3 are indexed by the bin, and Eq. (like) factorises over bins and mixtures), so a
+ * batch runs all bins of all mixtures together: one fused EM kernel per channel count (bins
+ * ordered longest first), the channel-count groups on concurrent streams, and optionally the
+ * whole job captured once as a CUDA graph and replayed with a single graph launch. Each
+ * mixture's results are those of the one-mixture entry points on the same inputs (the same
+ * kernels and the same fixed-order reductions; a bin's arithmetic does not depend on its
+ * neighbours).
+ *
+ * Packed layouts (C order, mixtures back to back in the order given):
+ *   y, x1, x2  complex64: mixture k's [F_k][N_k][M_k] block starts at element
+ *              sum_{k' < k} F_k' N_k' M_k'
+ *   v0, v      mixture k's [2][F_k][N_k] block starts at sum_{k' < k} 2 F_k' N_k'
+ *   S0         complex128: mixture k's [2][F_k][M_k][M_k] starts at sum_{k' < k} 2 F_k' M_k'^2
+ *   loglik     double [count][iters]
+ * ------------------------------------------------------------------------------------------ */
+typedef struct fca_batch fca_batch; /* opaque, allocated by fca_batch_init */
+
+enum { FCA_FORM_FAST = 0, FCA_FORM_CONVENTIONAL = 1 };
+
+typedef struct {
+  int32_t count;        /* number of mixtures, >= 1                                          */
+  const int32_t* M;     /* host int32 [count], 1..8; F, N: host int32 [count], >= 1, with   */
+  const int32_t* F;     /*   F_k N_k M_k < 2^31 for every mixture                           */
+  const int32_t* N;
+  int32_t location;     /* FCA_MEM_DEVICE or FCA_MEM_HOST, for y, v0 and S0                 */
+  const void* y;        /* complex64, packed (above)                                        */
+  const double* v0;     /* initial v_j^(0)(n,f) > 0, packed                                 */
+  const double* S0;     /* initial S_j^(0)(f), Hermitian positive definite, packed          */
+} fca_batch_problem;
+
+/* Allocate a batch for the shapes in *p and load it (as fca_batch_load). The device memory
+ * held is about 8 sum F N M (mixture copy) + 12 sum 2 F N (source powers) bytes plus small
+ * per-bin arrays. On failure *out is NULL and nothing stays allocated. */
+fca_status fca_batch_init(const fca_batch_problem* p, void* cuda_stream, fca_batch** out);
+
+/* Load new mixtures and initial parameters of the same shapes (count, M, F, N). Computes the
+ * positivity floor of v from the new y as fca_load does, clears a failed status and keeps the
+ * tuned launch shapes. Host v0 is staged through stream-ordered device memory. */
+fca_status fca_batch_load(fca_batch* b, const fca_batch_problem* p, void* cuda_stream);
+
+/* The whole job from the loaded initial parameters: 0 <= iters <= 65535 EM iterations of `form`
+ * (FCA_FORM_FAST: Algorithm 1, from the generalised eigenproblem of S0; FCA_FORM_CONVENTIONAL:
+ * Sec. 2) for every mixture, then the posterior means of Algorithm 1's output (the E-step of
+ * iteration L-1; the initial parameters when iters = 0) into the packed device buffers x1_dev,
+ * x2_dev. loglik_dev: NULL or device double [count][iters] (Eq. (like) at the parameters of
+ * each iteration, per mixture). v_dev: NULL or device float, packed like v0: v after the last
+ * iteration. The job depends only on the loaded inputs, so it can be run again.
+ * use_graph != 0: the first call with given (form, iters, buffers) captures the job into a CUDA
+ * graph (on an internal stream; the call must not itself be inside a stream capture) and
+ * every call launches that graph on cuda_stream; other arguments re-capture. Asynchronous. */
+fca_status fca_batch_run(fca_batch* b, int32_t form, int32_t iters, double* loglik_dev,
+                         void* x1_dev, void* x2_dev, float* v_dev, int32_t use_graph,
+                         void* cuda_stream);
+
+/* Autotune the FastFCA launch shape of every channel-count group: threads per CTA (64, 128,
+ * 256) and how much shared memory a CTA may take to keep its bin's mixture and source powers
+ * on chip (bins that do not fit stream them from memory every iteration). Each candidate runs
+ * min(iters, 3) iterations on a sample of the group's bins spanning its range of lengths;
+ * the fastest is kept for later runs. Synchronises the stream. Overwrites the EM state (not the
+ * loaded inputs), so run it before fca_batch_run, not between a run and the use of its outputs. */
+fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* cuda_stream);
+
+/* Launch shape of the channel-count group M: its number of bins, threads per CTA and the
+ * dynamic shared memory per CTA. FCA_ERR_ARG if no mixture has M channels. */
+fca_status fca_batch_shape(const fca_batch* b, int32_t M, int32_t* bins, int32_t* threads,
+                           int32_t* res_bytes);
+
+/* Synchronise the stream and return the first device-side error of this batch. After an
+ * error every run returns FCA_ERR_STATE until fca_batch_load. */
+fca_status fca_batch_sync_status(fca_batch* b, void* cuda_stream);
+
+/* Release the batch (synchronises the device first). NULL is a no-op. */
+void fca_batch_free(fca_batch* b);
 
 /* Static description of a status code. */
 const char* fca_status_string(fca_status st);

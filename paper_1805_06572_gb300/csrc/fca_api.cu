@@ -39,6 +39,7 @@ struct DeviceGuard {  // make the state's device current for the duration of a c
 
 struct fca_state {
   int M, F, N, storage, device;
+  int N_cap;  // frames the device buffers were sized for (fca_init); N <= N_cap
   size_t FN, MM;
   void* y;
   float* g;
@@ -167,7 +168,7 @@ const char* fca_version(void) { return "fca-gb300 1.0 (sm_103a)"; }
 
 fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
   if (!s || !problem_ok(p)) return FCA_ERR_ARG;
-  if (p->M != s->M || p->F != s->F || p->N != s->N || p->storage != s->storage) return FCA_ERR_ARG;
+  if (p->M != s->M || p->F != s->F || p->N > s->N_cap || p->storage != s->storage) return FCA_ERR_ARG;
   DeviceGuard guard(s->device);
   if (p->location == FCA_MEM_DEVICE) {
     if (!device_pointer(p->y, s->device) || !device_pointer(p->v0, s->device) ||
@@ -176,6 +177,8 @@ fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
       return FCA_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  s->N = p->N;
+  s->FN = (size_t)s->F * s->N;
   const size_t ybytes = s->FN * s->M * (s->storage ? 4 : 8);
   FCA_CHECK_CUDA(cudaMemcpyAsync(s->y, p->y, ybytes, cudaMemcpyDefault, st));
   if (s->storage == FCA_STORE_F16_SCALED) {
@@ -185,7 +188,7 @@ fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
   FCA_CHECK_CUDA(cudaMemcpyAsync(s->S, p->S0, 2 * s->F * s->MM * sizeof(double2), cudaMemcpyDefault, st));
   const double* v0 = p->v0;
   if (p->location == FCA_MEM_HOST) {
-    if (!s->v0_stage) FCA_CHECK_CUDA(dalloc(&s->v0_stage, 2 * s->FN));
+    if (!s->v0_stage) FCA_CHECK_CUDA(dalloc(&s->v0_stage, 2 * (size_t)s->F * s->N_cap));
     FCA_CHECK_CUDA(cudaMemcpyAsync(s->v0_stage, p->v0, 2 * s->FN * sizeof(double), cudaMemcpyDefault, st));
     v0 = s->v0_stage;
   }
@@ -211,6 +214,7 @@ fca_status fca_init(const fca_problem* p, void* stream, fca_state** out) {
   s->M = p->M;
   s->F = p->F;
   s->N = p->N;
+  s->N_cap = p->N;
   s->storage = p->storage;
   s->device = dev;
   s->FN = (size_t)p->F * p->N;
@@ -285,13 +289,16 @@ fca_status fca_em_fast(fca_state* s, int32_t iters, double* loglik_dev, void* st
     s->form = kFormP;
   }
   FastEmArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.F = s->F;
   a.N = s->N;
   a.iters = iters;
-  a.resident = em_resident(s->M, s->storage, s->N) ? 1 : 0;
+  a.res_bytes = em_resident(s->M, s->storage, s->N) ? (int)em_dyn_smem(s->M, s->storage, s->N) : 0;
+  a.bins = nullptr;
   a.y = s->y;
   a.ginv = s->ginv;
   a.vfloor = s->vfloor;
+  a.v_in = s->v;
   a.v = s->v;
   a.v_prev = s->v_prev;
   a.P = s->P;
@@ -329,15 +336,19 @@ fca_status fca_em_conventional(fca_state* s, int32_t iters, double* loglik_dev, 
     s->form = kFormS;
   }
   ConvEmArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.F = s->F;
   a.N = s->N;
   a.iters = iters;
-  a.resident = em_resident(s->M, s->storage, s->N) ? 1 : 0;
+  a.res_bytes = em_resident(s->M, s->storage, s->N) ? (int)em_dyn_smem(s->M, s->storage, s->N) : 0;
+  a.bins = nullptr;
   a.y = s->y;
   a.ginv = s->ginv;
   a.vfloor = s->vfloor;
+  a.v_in = s->v;
   a.v = s->v;
   a.v_prev = s->v_prev;
+  a.S_in = s->S;
   a.S = s->S;
   a.S_prev = s->S_prev;
   a.llf = s->llf;
@@ -371,6 +382,7 @@ fca_status fca_separate(fca_state* s, void* x1_dev, void* x2_dev, int32_t mode, 
     pa.lam32 = s->sep_lam;
     FCA_CHECK_CUDA(counted(launch_sep_prep(s->M, pa, st)));
     SepFastArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.F = s->F;
     a.N = s->N;
     a.y = s->y;
@@ -384,6 +396,7 @@ fca_status fca_separate(fca_state* s, void* x1_dev, void* x2_dev, int32_t mode, 
     FCA_CHECK_CUDA(counted(launch_sep_fast(s->M, s->storage, a, st)));
   } else {
     SepConvArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.F = s->F;
     a.N = s->N;
     a.y = s->y;

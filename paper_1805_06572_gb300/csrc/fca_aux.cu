@@ -142,14 +142,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) from_P_kernel(const ParamAr
 }
 
 template <int M, int ST>
-__global__ void __launch_bounds__(256) prepare_kernel(int F, int N, const void* y, const float* ginv,
+__global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void* y, const float* ginv,
                                                       const double* v0, float* v, float* vfloor,
-                                                      int* status) {
+                                                      int* status, const BinDesc* bins) {
   using E = typename Elem<ST>::T;
   __shared__ double part[8];
   __shared__ float vf_s;
-  const int f = blockIdx.x, tid = threadIdx.x;
-  const E* yf = reinterpret_cast<const E*>(y) + (size_t)f * N * M;
+  const int tid = threadIdx.x;
+  int f, N;
+  size_t yoff, voff[2];
+  if (bins) {
+    const BinDesc d = bins[blockIdx.x];
+    f = d.b;
+    N = d.N;
+    yoff = (size_t)d.y_off;
+    voff[0] = (size_t)d.v1_off;
+    voff[1] = (size_t)d.v2_off;
+  } else {
+    f = blockIdx.x;
+    N = N0;
+    yoff = (size_t)f * N * M;
+    voff[0] = (size_t)f * N;
+    voff[1] = (size_t)F * N + voff[0];
+  }
+  const E* yf = reinterpret_cast<const E*>(y) + yoff;
   float s = 0.f;
   for (int i = tid; i < N * M; i += 256) s += cabs2(decode(yf[i]));
   s = warp_sum(s);
@@ -169,7 +185,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N, const void* 
   int bad = 0;
   for (int j = 0; j < 2; ++j)
     for (int n = tid; n < N; n += 256) {
-      const size_t i = ((size_t)j * F + f) * N + n;
+      const size_t i = voff[j] + n;
       const double x = v0[i];
       bad |= !isfinite(x);
       v[i] = fmaxf((float)x, vf);
@@ -189,6 +205,24 @@ __global__ void ll_reduce_kernel(int F, const double* llf, double* ll) {
     __syncthreads();
   }
   if (tid == 0) ll[l] = part[0];
+}
+
+// One CTA per (iteration, mixture): the mixture's log-likelihood is the sum over its bins
+// (Eq. (like) factorises over frequencies), in a fixed order.
+__global__ void ll_ranges_kernel(int F, const double* llf, const int* b0, const int* nb,
+                                 const int* mix_id, int iters, double* out) {
+  __shared__ double part[128];
+  const int k = blockIdx.x, l = blockIdx.y, tid = threadIdx.x;
+  const int lo = b0[k], n = nb[k];
+  double s = 0.0;
+  for (int i = tid; i < n; i += 128) s += llf[(size_t)l * F + lo + i];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 64; o >= 1; o >>= 1) {
+    if (tid < o) part[tid] += part[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) out[(size_t)mix_id[k] * iters + l] = part[0];
 }
 
 __global__ void invert_scale_kernel(int F, const float* g, float* ginv) {
@@ -212,26 +246,38 @@ __global__ void invert_scale_kernel(int F, const float* g, float* ginv) {
 
 cudaError_t launch_gevd_from_S(int M, const ParamArgs& a, cudaStream_t st) {
   const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (grid <= 0) return cudaSuccess;
   FCA_DISPATCH_M(M, (gevd_from_S_kernel<kM><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
 }
 
 cudaError_t launch_S_from_P(int M, const ParamArgs& a, cudaStream_t st) {
   const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (grid <= 0) return cudaSuccess;
   FCA_DISPATCH_M(M, (from_P_kernel<kM, 0><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
 }
 
 cudaError_t launch_sep_prep(int M, const ParamArgs& a, cudaStream_t st) {
   const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (grid <= 0) return cudaSuccess;
   FCA_DISPATCH_M(M, (from_P_kernel<kM, 1><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
 }
 
 cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
-                           const double* v0, float* v, float* vfloor, int* status, cudaStream_t st) {
+                           const double* v0, float* v, float* vfloor, int* status, cudaStream_t st,
+                           const BinDesc* bins) {
+  if (F <= 0) return cudaSuccess;
   if (storage) {
-    FCA_DISPATCH_M(M, (prepare_kernel<kM, 1><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status)); return cudaGetLastError())
+    FCA_DISPATCH_M(M, (prepare_kernel<kM, 1><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins)); return cudaGetLastError())
   } else {
-    FCA_DISPATCH_M(M, (prepare_kernel<kM, 0><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status)); return cudaGetLastError())
+    FCA_DISPATCH_M(M, (prepare_kernel<kM, 0><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins)); return cudaGetLastError())
   }
+}
+
+cudaError_t launch_ll_ranges(int nmix, int iters, int F, const double* llf, const int* b0,
+                             const int* nb, const int* mix_id, double* out, cudaStream_t st) {
+  if (nmix <= 0 || iters <= 0) return cudaSuccess;
+  ll_ranges_kernel<<<dim3(nmix, iters), 128, 0, st>>>(F, llf, b0, nb, mix_id, iters, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ll_reduce(int F, int iters, const double* llf, double* ll, cudaStream_t st) {

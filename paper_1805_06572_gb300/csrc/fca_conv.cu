@@ -71,7 +71,9 @@ __device__ bool warp_hpd_inverse(WarpLA& la, const double2 (*S)[kMaxM], float2 (
 
 __host__ __device__ constexpr int conv_min_blocks(int M) { return M <= 3 ? 4 : (M <= 4 ? 3 : 2); }
 
-template <int M, int ST, int NT>
+// kB: the CTA's bin comes from the descriptor table a.bins (a batch); otherwise bin
+// f = blockIdx.x of one mixture with v_in == v and S_in == S.
+template <int M, int ST, int NT, bool kB>
 __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const ConvEmArgs a) {
   using E = typename Elem<ST>::T;
   constexpr int NW = NT / 32;
@@ -82,30 +84,47 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
   __shared__ Sh sh;
   extern __shared__ __align__(16) unsigned char dyn[];
 
-  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int N = a.N, F = a.F;
-  const size_t fN = (size_t)f * N;
-  const E* yg = reinterpret_cast<const E*>(a.y) + fN * M;
-  float* vg1 = a.v + fN;
-  float* vg2 = a.v + (size_t)F * N + fN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int F = a.F;
+  int f, N;
+  size_t yoff, v1off, v2off;
+  if constexpr (kB) {
+    const BinDesc d = a.bins[blockIdx.x];
+    f = d.b;
+    N = d.N;
+    yoff = (size_t)d.y_off;
+    v1off = (size_t)d.v1_off;
+    v2off = (size_t)d.v2_off;
+  } else {
+    f = blockIdx.x;
+    N = a.N;
+    yoff = (size_t)f * N * M;
+    v1off = (size_t)f * N;
+    v2off = (size_t)F * N + v1off;
+  }
+  const E* yg = reinterpret_cast<const E*>(a.y) + yoff;
+  float* vg1 = a.v + v1off;
+  const int dv2 = (int)(v2off - v1off);  // v_2(., bin) lies dv2 floats after v_1(., bin)
+  const ptrdiff_t d_in = kB ? a.v_in - a.v : 0, d_prev = a.v_prev - a.v;
   E* ys = reinterpret_cast<E*>(dyn);
   const size_t ybytes = ((size_t)N * M * sizeof(E) + 15) & ~(size_t)15;
   float* vs = reinterpret_cast<float*>(dyn + ybytes);
-  const bool res = a.resident != 0;
+  // One mixture: the launch reserves exactly its bins' need, or nothing.
+  const bool res = kB ? em_bin_smem(M, ST, N) <= (size_t)a.res_bytes : a.res_bytes != 0;
   const E* ysrc = res ? ys : yg;
   float* v1p = res ? vs : vg1;
-  float* v2p = res ? vs + N : vg2;
+  float* v2p = res ? vs + N : (kB ? vg1 + dv2 : a.v + (size_t)F * N + (size_t)f * N);
   const float vf = a.vfloor[f];
   const float gi = (ST == 1) ? a.ginv[f] : 1.f;
 
   for (int e = tid; e < 2 * MM; e += NT) {
     const int j = e / MM, r = e % MM;
-    sh.S[j][r / M][r % M] = a.S[((size_t)j * F + f) * MM + r];
+    sh.S[j][r / M][r % M] = (kB ? a.S_in : a.S)[((size_t)j * F + f) * MM + r];
   }
   if (tid == 0) sh.fail = 0;
   if (res) {
     const size_t bytes = (size_t)N * M * sizeof(E);
-    if ((bytes & 15) == 0) {
+    if ((bytes & 15) == 0 && (!kB || (reinterpret_cast<uintptr_t>(yg) & 15) == 0)) {
       const uint4* src = reinterpret_cast<const uint4*>(yg);
       uint4* dst = reinterpret_cast<uint4*>(ys);
       for (size_t i = tid; i < bytes / 16; i += NT) dst[i] = src[i];
@@ -115,8 +134,15 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
       for (size_t i = tid; i < bytes / 4; i += NT) dst[i] = src[i];
     }
     for (int n = tid; n < N; n += NT) {
-      vs[n] = vg1[n];
-      vs[N + n] = vg2[n];
+      vs[n] = vg1[d_in + n];
+      vs[N + n] = vg1[d_in + dv2 + n];
+    }
+  } else if (kB && d_in != 0) {
+    // Streaming bin with separate initial values: start the working copy from them (each
+    // thread copies the frames it updates in the iterations below).
+    for (int n = tid; n < N; n += NT) {
+      vg1[n] = vg1[d_in + n];
+      vg1[dv2 + n] = vg1[d_in + dv2 + n];
     }
   }
   __syncthreads();
@@ -151,8 +177,13 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
       for (int i = 0; i < M; ++i) yv[i] = cscale(yv[i], gi);
       const float v1 = v1p[n], v2 = v2p[n];
       if (last) {
-        a.v_prev[fN + n] = v1;
-        a.v_prev[(size_t)F * N + fN + n] = v2;
+        if constexpr (kB) {
+          vg1[d_prev + n] = v1;
+          vg1[d_prev + dv2 + n] = v2;
+        } else {
+          a.v_prev[(size_t)f * N + n] = v1;
+          a.v_prev[(size_t)F * N + (size_t)f * N + n] = v2;
+        }
       }
       // Cholesky of Rx = v1 S1 + v2 S2 (lower triangle), in registers.
       float2 L[M][M];
@@ -326,7 +357,7 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
   if (res) {
     for (int n = tid; n < N; n += NT) {
       vg1[n] = vs[n];
-      vg2[n] = vs[N + n];
+      vg1[dv2 + n] = vs[N + n];
     }
   }
 }
@@ -336,20 +367,39 @@ template <int M, int ST>
 __global__ void __launch_bounds__(256) sep_conv_kernel(const SepConvArgs a) {
   using E = typename Elem<ST>::T;
   __shared__ float2 S32[2][M][M];
-  const int f = blockIdx.y, tid = threadIdx.x;
+  const int tid = threadIdx.x;
+  int f, N;
+  size_t yoff, xoff, v1off, v2off;
+  if (a.bins) {
+    const BinDesc d = a.bins[blockIdx.x];
+    f = d.b;
+    N = d.N;
+    yoff = (size_t)d.y_off;
+    xoff = (size_t)d.x_off;
+    v1off = (size_t)d.v1_off;
+    v2off = (size_t)d.v2_off;
+  } else {
+    f = blockIdx.x;
+    N = a.N;
+    yoff = (size_t)f * N * M;
+    xoff = yoff;
+    v1off = (size_t)f * N;
+    v2off = (size_t)a.F * N + v1off;
+  }
+  if (blockIdx.y * 256 >= N) return;  // whole CTA past this bin's frames
   const size_t MM = (size_t)M * M;
   if (tid < 2 * M * M) {
     const int j = tid / (M * M), r = tid % (M * M);
     S32[j][r / M][r % M] = z2c(a.S[((size_t)j * a.F + f) * MM + r]);
   }
   __syncthreads();
-  const int n = blockIdx.x * 256 + tid;
-  if (n >= a.N) return;
-  const size_t b = (size_t)f * a.N + n;
+  const int n = blockIdx.y * 256 + tid;
+  if (n >= N) return;
+  const size_t b = xoff + (size_t)n * M;
   const float gi = (ST == 1) ? a.ginv[f] : 1.f;
   float2 yv[M];
-  load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + b * M, yv);
-  const float v1 = a.v[b], v2 = a.v[(size_t)a.F * a.N + b];
+  load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + yoff + (size_t)n * M, yv);
+  const float v1 = a.v[v1off + n], v2 = a.v[v2off + n];
   float2 L[M][M];
   int bad = 0;
 #pragma unroll
@@ -390,16 +440,19 @@ __global__ void __launch_bounds__(256) sep_conv_kernel(const SepConvArgs a) {
       s1 = cfma(S32[0][i][k], u[k], s1);
       s2 = cfma(S32[1][i][k], u[k], s2);
     }
-    a.x1[b * M + i] = cscale(s1, v1);
-    a.x2[b * M + i] = cscale(s2, v2);
+    a.x1[b + i] = cscale(s1, v1);
+    a.x2[b + i] = cscale(s2, v2);
   }
 }
 
 // ------------------------------------------------------------------ host-side launchers
 template <int M, int ST, int NT>
 static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
-  size_t dyn = a.resident ? em_dyn_smem(M, ST, a.N) : 0;
-  auto k = conv_em_kernel<M, ST, NT>;
+  const size_t dyn = (size_t)a.res_bytes;
+  const int grid = a.bins ? a.nbins : a.F;
+  if (grid <= 0) return cudaSuccess;
+  if (a.bins && ST != 0) return cudaErrorInvalidValue;  // batches hold complex64 mixtures
+  auto k = a.bins ? conv_em_kernel<M, 0, NT, true> : conv_em_kernel<M, ST, NT, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
@@ -407,7 +460,7 @@ static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
-  k<<<a.F, NT, dyn, st>>>(a);
+  k<<<grid, NT, dyn, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -437,7 +490,8 @@ cudaError_t launch_conv_em(int M, int storage, const ConvEmArgs& a, cudaStream_t
 
 template <int M, int ST>
 static cudaError_t launch_sep_conv_m(const SepConvArgs& a, cudaStream_t st) {
-  dim3 grid((a.N + 255) / 256, a.F);
+  dim3 grid(a.F, (a.N + 255) / 256);  // bins on x (no 65535 limit), frame chunks on y
+  if (a.N <= 0 || a.F <= 0) return cudaSuccess;
   sep_conv_kernel<M, ST><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }

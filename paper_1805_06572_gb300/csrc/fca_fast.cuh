@@ -1,0 +1,514 @@
+// FastFCA (Ito, Araki, Nakatani, arXiv 1805.06572, Sec. 3, Algorithm 1) on sm_103a.
+//
+// One CTA owns one frequency bin f for all L iterations (every quantity of the EM is
+// indexed by f and Eq. (like) factorises over f, so CTAs never communicate). Per iteration:
+//   bin pass (FP32, one thread per time-frequency point, frames strided over the CTA):
+//     yt = P^H y                                        Eq. (tildey)
+//     d_i = v1 lam_i + v2, mut1 = v1 lam yt / d,        Eq. (MMSEtilde)
+//       mut2 = v2 yt / d
+//     c_i = v1 v2 lam_i / d_i                           Eq. (updatePhitildeeff), diagonal
+//     v1' = (1/M) sum_i (|mut1_i|^2 + c_i) / lam_i      Eq. (updateveff)
+//     v2' = (1/M) sum_i (|mut2_i|^2 + c_i)
+//     St_j += (mut_j mut_j^H + diag(c)) / v_j'          Eq. (updateStildeeff), partial sums
+//     log-likelihood terms log d_i + |yt_i|^2 / d_i     Eq. (like) in the transformed basis
+//   CTA reduction: per-lane FP32 partials -> warp transpose-reduction (FP32) -> cross-warp
+//     merge in FP64, in a fixed order (bitwise reproducible);
+//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8) and the next
+//     basis P^H for the bin pass; meanwhile warp 1 does the previous iteration's FP64
+//     bookkeeping: P <- P Q (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)),
+//     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use), and the
+//     previous iteration's log-likelihood.
+// The log-likelihood of iteration l uses log det Rx = sum_i log d_i + log det S2 and
+// y^H Rx^-1 y = sum_i |yt_i|^2 / d_i, which follow from Rx = P^-H (v1 Lam + v2 I) P^-1.
+// The mixture and v stay in shared memory across iterations when they fit.
+#pragma once
+#include "fca_dev.cuh"
+#include "fca_internal.h"
+
+namespace fca {
+
+template <int M, int NW>
+struct FastShared {
+  static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
+  float red[NW][V];
+  double2 P[kMaxM][kMaxM];      // basis P (FP64)
+  float2 P32[kMaxM][kMaxM];     // P rounded to FP32
+  float2 PH[M][M];              // FP32 P^H (times the decode scale) used by the bin pass
+  float lam[M], ilam[M];
+  double lam64[kMaxM];
+  // Double-buffered results of an iteration's eigensolve, consumed by the deferred FP64
+  // bookkeeping one iteration later.
+  float2 Q[2][kMaxM][kMaxM];
+  float2 U[2][kMaxM][kMaxM];
+  float sig[2][kMaxM];
+  float ldL[2];                 // 2 sum log(1/L_ii): log|det Q|^2 = ldL + log|det U|^2
+  double llt[2][2];             // sum log d, sum p/d of the iteration
+  double logdetS2;
+  int fail;          // read by every thread after a barrier; written only before one
+  int fail_pending;  // set by the deferred bookkeeping, folded into `fail` by warp 0
+  WarpLA la;
+};
+
+__host__ __device__ constexpr int pair_index(int M, int i, int k) {  // i < k
+  return i * (M - 1) - i * (i - 1) / 2 + (k - i - 1);
+}
+
+// Resident CTAs per SM the register budget is sized for (one CTA per frequency bin: more
+// CTAs per SM hide each CTA's serial per-bin eigensolver behind the others' bin passes).
+__host__ __device__ constexpr int fast_min_blocks(int M) { return M <= 4 ? 4 : (M <= 6 ? 3 : 2); }
+// The same register budget per thread for every CTA size.
+__host__ __device__ constexpr int fast_min_blocks(int M, int NT) {
+  return fast_min_blocks(M) * 128 / NT > 0 ? fast_min_blocks(M) * 128 / NT : 1;
+}
+
+// Value v of the per-warp partial-sum vector -> the Hermitian matrix entry it belongs to:
+// Gram g (0, 1), row i, column k (i <= k), and part (0 = real, 1 = imaginary).
+template <int M>
+__device__ __forceinline__ void value_entry(int v, int* g, int* i, int* k, int* part) {
+  constexpr int MM = M * M;
+  *g = v / MM;
+  int r = v - *g * MM;
+  if (r < M) {
+    *i = *k = r;
+    *part = 0;
+    return;
+  }
+  r -= M;
+  *part = r & 1;
+  int pr = r >> 1, row = 0;
+  while (pr >= M - 1 - row) {
+    pr -= M - 1 - row;
+    ++row;
+  }
+  *i = row;
+  *k = row + 1 + pr;
+}
+
+// Deferred FP64 bookkeeping of iteration `it` (one warp): P <- P Q (Eq. (updatePeff)),
+// Lambda <- Sigma (Eq. (updateLambdaeff)), the log-likelihood of iteration it (at its own
+// parameters), log det S2 of the next iteration, and the parameters of iteration L-1.
+template <int M, typename Sh>
+__device__ void fast_deferred(Sh& sh, const FastEmArgs& a, int f, int N, int it, int lane) {
+  constexpr int MM = M * M;
+  const int b = it & 1;
+  warp_update_basis_q<M>(sh.P, sh.Q[b], lane);
+  for (int e = lane; e < MM; e += 32) sh.P32[e / M][e % M] = z2c(sh.P[e / M][e % M]);
+  if (lane < M) sh.lam64[lane] = (double)sh.sig[b][lane];
+  if (lane == 0) {
+    const double ll = -(double)N * M * 1.1447298858494002 - sh.llt[b][0] - sh.llt[b][1] -
+                      (double)N * sh.logdetS2;
+    a.llf[(size_t)it * a.F + f] = ll;
+    if (!isfinite(ll)) {
+      set_status(a.status, kErrNonFinite);
+      sh.fail_pending = kErrNonFinite;
+    }
+  }
+  // log det S2 = -log|det P|^2 and P <- P Q: subtract log|det Q|^2 of the Q applied.
+  const double ldQ = (double)sh.ldL[b] + unitarity_defect<M>(sh.U[b], lane);
+  if (lane == 0) sh.logdetS2 -= ldQ;
+  __syncwarp();
+  if (it == a.iters - 2) {  // the parameters of iteration L-1
+    for (int e = lane; e < MM; e += 32) a.P_prev[(size_t)f * MM + e] = sh.P[e / M][e % M];
+    if (lane < M) a.lam_prev[(size_t)f * M + lane] = sh.lam64[lane];
+    if (lane == 0) a.logdetS2_prev[f] = sh.logdetS2;
+  }
+  __syncwarp();
+}
+
+// kB: the CTA's bin comes from the descriptor table a.bins (a batch); otherwise bin
+// f = blockIdx.x of one mixture with the [F][N][M] / [2][F][N] layouts and v_in == v.
+template <int M, int ST, int NT, bool kB>
+__global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(const FastEmArgs a) {
+  using E = typename Elem<ST>::T;
+  constexpr int NW = NT / 32;
+  static_assert(NW >= 2, "the deferred bookkeeping runs on warp 1");
+  using Sh = FastShared<M, NW>;
+  constexpr int V = Sh::V;
+  constexpr int MM = M * M;
+  constexpr bool kHoist = (M <= 4);
+  __shared__ Sh sh;
+  extern __shared__ __align__(16) unsigned char dyn[];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int f, N;
+  size_t yoff, v1off, v2off;
+  if constexpr (kB) {
+    const BinDesc d = a.bins[blockIdx.x];
+    f = d.b;
+    N = d.N;
+    yoff = (size_t)d.y_off;
+    v1off = (size_t)d.v1_off;
+    v2off = (size_t)d.v2_off;
+  } else {
+    f = blockIdx.x;
+    N = a.N;
+    yoff = (size_t)f * N * M;
+    v1off = (size_t)f * N;
+    v2off = (size_t)a.F * N + v1off;
+  }
+  const E* yg = reinterpret_cast<const E*>(a.y) + yoff;
+  float* vg1 = a.v + v1off;
+  const int dv2 = (int)(v2off - v1off);  // v_2(., bin) lies dv2 floats after v_1(., bin)
+  // The initial and previous source powers sit at the same offsets in their own arrays; the
+  // distances between the arrays are kernel parameters (no registers held in the hot loop).
+  const ptrdiff_t d_in = kB ? a.v_in - a.v : 0, d_prev = a.v_prev - a.v;
+  E* ys = reinterpret_cast<E*>(dyn);
+  const size_t ybytes = ((size_t)N * M * sizeof(E) + 15) & ~(size_t)15;
+  float* vs = reinterpret_cast<float*>(dyn + ybytes);
+  // One mixture: the launch reserves exactly its bins' need, or nothing.
+  const bool res = kB ? em_bin_smem(M, ST, N) <= (size_t)a.res_bytes : a.res_bytes != 0;
+  const E* ysrc = res ? ys : yg;
+  float* v1p = res ? vs : vg1;
+  float* v2p = res ? vs + N : vg1 + dv2;
+  const float vf = a.vfloor[f];
+  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+  const double invN = 1.0 / (double)N;
+
+  if (tid < MM) {
+    const double2 p = a.P[(size_t)f * MM + tid];
+    sh.P[tid / M][tid % M] = p;
+    sh.P32[tid / M][tid % M] = z2c(p);
+  }
+  if (tid < M) {
+    const double l = a.lam[(size_t)f * M + tid];
+    sh.lam64[tid] = l;
+    sh.lam[tid] = (float)l;
+    sh.ilam[tid] = 1.f / (float)l;
+  }
+  if (tid == 0) {
+    sh.logdetS2 = a.logdetS2[f];
+    sh.fail = 0;
+    sh.fail_pending = 0;
+  }
+  if (res) {
+    const size_t bytes = (size_t)N * M * sizeof(E);
+    if ((bytes & 15) == 0 && (!kB || (reinterpret_cast<uintptr_t>(yg) & 15) == 0)) {
+      const uint4* src = reinterpret_cast<const uint4*>(yg);
+      uint4* dst = reinterpret_cast<uint4*>(ys);
+      for (size_t i = tid; i < bytes / 16; i += NT) dst[i] = src[i];
+    } else {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(yg);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(ys);
+      for (size_t i = tid; i < bytes / 4; i += NT) dst[i] = src[i];
+    }
+    for (int n = tid; n < N; n += NT) {
+      vs[n] = vg1[d_in + n];
+      vs[N + n] = vg1[d_in + dv2 + n];
+    }
+  } else if (kB && d_in != 0) {
+    // Streaming bin with separate initial values: start the working copy from them (each
+    // thread copies the frames it updates in the iterations below).
+    for (int n = tid; n < N; n += NT) {
+      vg1[n] = vg1[d_in + n];
+      vg1[dv2 + n] = vg1[d_in + dv2 + n];
+    }
+  }
+  __syncthreads();
+  if (tid < MM) {
+    const int i = tid / M, m = tid % M;
+    const double2 p = sh.P[m][i];
+    sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
+  }
+  if (a.iters == 1) {  // the parameters of iteration L-1 are the initial ones
+    if (tid < MM) a.P_prev[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
+    if (tid < M) a.lam_prev[(size_t)f * M + tid] = sh.lam64[tid];
+    if (tid == 0) a.logdetS2_prev[f] = sh.logdetS2;
+  }
+  __syncthreads();
+
+  int done = 0;  // iterations whose bin pass and eigensolve completed
+  for (int it = 0; it < a.iters; ++it) {
+    const bool last = (it == a.iters - 1);
+    const int b = it & 1;
+    using RS = RedShape<V>;
+    float acc[RS::NA];
+#pragma unroll
+    for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
+    float2 ph[kHoist ? M : 1][kHoist ? M : 1];
+    float lamr[M], ilamr[M];
+    if constexpr (kHoist) {
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m) ph[i][m] = sh.PH[i][m];
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      lamr[i] = sh.lam[i];
+      ilamr[i] = sh.ilam[i];
+    }
+
+    for (int n = tid; n < N; n += NT) {
+      float2 yv[M];
+      load_bin<M, ST>(ysrc + (size_t)n * M, yv);
+      const float v1 = v1p[n], v2 = v2p[n];
+      if (last) {
+        vg1[d_prev + n] = v1;
+        vg1[d_prev + dv2 + n] = v2;
+      }
+      float2 yt[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        float2 s;
+        if constexpr (kHoist) {
+          s = cmul(ph[i][0], yv[0]);
+#pragma unroll
+          for (int m = 1; m < M; ++m) s = cfma(ph[i][m], yv[m], s);
+        } else {
+          s = cmul(sh.PH[i][0], yv[0]);
+#pragma unroll
+          for (int m = 1; m < M; ++m) s = cfma(sh.PH[i][m], yv[m], s);
+        }
+        yt[i] = s;
+      }
+      // With r_i = 1/d_i, t_i = lam_i r_i and q_i = |yt_i|^2 r_i^2 (d_i = v1 lam_i + v2):
+      //   v1' = (v1/M)(v1 sum lam_i q_i + v2 sum r_i)     (Eq. (updateveff), j = 1)
+      //   v2' = (v2/M)(v2 sum q_i + v1 sum t_i)           (Eq. (updateveff), j = 2)
+      //   mut1_i / sqrt(v1') = (v1 / sqrt(v1')) t_i yt_i, mut2_i / sqrt(v2') = (v2 / sqrt(v2')) r_i yt_i
+      //   c_i / v_j' = (v1 v2 / v_j') t_i                 (Eq. (updatePhitildeeff))
+      float r[M], t[M], pp[M];
+      float sA = 0.f, sB = 0.f, sC = 0.f, sD = 0.f, ql = 0.f;
+      LogProd lp;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const float d = fmaf(v1, lamr[i], v2);
+        r[i] = __fdividef(1.f, d);
+        pp[i] = cabs2(yt[i]);
+        t[i] = lamr[i] * r[i];
+        const float pr = pp[i] * r[i];
+        const float q = pr * r[i];
+        sA = fmaf(lamr[i], q, sA);
+        sB += r[i];
+        sC += q;
+        sD += t[i];
+        ql += pr;
+        lp.mul(d);
+      }
+      const float v1n = fmaxf((v1 * (1.f / M)) * fmaf(v1, sA, v2 * sB), vf);
+      const float v2n = fmaxf((v2 * (1.f / M)) * fmaf(v2, sC, v1 * sD), vf);
+      v1p[n] = v1n;
+      v2p[n] = v2n;
+      const float rs1 = rsqrtf(v1n), rs2 = rsqrtf(v2n);
+      const float a1 = v1 * rs1, a2 = v2 * rs2;
+      const float v12 = v1 * v2;
+      const float k1 = v12 * (rs1 * rs1), k2 = v12 * (rs2 * rs2);
+      float s1[M], s2[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        s1[i] = a1 * t[i];
+        s2[i] = a2 * r[i];
+        acc[i] = fmaf(s1[i] * s1[i], pp[i], fmaf(k1, t[i], acc[i]));
+        acc[MM + i] = fmaf(s2[i] * s2[i], pp[i], fmaf(k2, t[i], acc[MM + i]));
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) {
+          const int o = M + 2 * pair_index(M, i, k);
+          const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
+          const float w1 = s1[i] * s1[k], w2 = s2[i] * s2[k];
+          acc[o] = fmaf(w1, z.x, acc[o]);
+          acc[o + 1] = fmaf(w1, z.y, acc[o + 1]);
+          acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
+          acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
+        }
+      acc[2 * MM] += lp.log_fast();
+      acc[2 * MM + 1] += ql;
+    }
+
+    warp_reduce_store<V>(acc, lane, sh.red[warp]);
+    __syncthreads();
+    // Merge the warp partials in a fixed order: Gram entries in FP32 (they feed the FP32
+    // eigensolver), the two log-likelihood sums with a compensated two-float sum kept in
+    // FP64. One value per thread.
+    for (int e = tid; e < V; e += NT) {
+      if (e < 2 * MM) {
+        float sv[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sv[w] = sh.red[w][e];
+#pragma unroll
+        for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+          for (int w = 0; w < h; ++w) sv[w] += sv[w + h];
+        const float val = sv[0] * (float)invN;
+        int g, i, k, part;
+        value_entry<M>(e, &g, &i, &k, &part);
+        float2(*D)[kMaxM] = g ? sh.la.L : sh.la.A;
+        if (i == k) {
+          D[i][i] = make_float2(val, 0.f);
+        } else if (part == 0) {
+          D[i][k].x = val;
+          D[k][i].x = val;
+        } else {
+          D[i][k].y = val;
+          D[k][i].y = -val;
+        }
+      } else {
+        float hi = sh.red[0][e], lo = 0.f;
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {  // TwoSum (Knuth): hi + lo = exact running sum
+          const float x = sh.red[w][e];
+          const float t = hi + x;
+          const float bp = t - hi;
+          lo += (hi - (t - bp)) + (x - bp);
+          hi = t;
+        }
+        sh.llt[b][e - 2 * MM] = (double)hi + (double)lo;
+      }
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+      float ldL = 0.f;
+      int rc;
+      if constexpr (M <= 4) {
+        rc = kOk;
+        if (lane == 0) rc = lane_gevd<M>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL, 2.0e-7f, 30);
+        rc = __shfl_sync(0xffffffffu, rc, 0);
+        __syncwarp();
+      } else {
+        rc = warp_gevd_fast<M>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL);
+      }
+      if (lane == 0) sh.ldL[b] = ldL;
+      if (rc != kOk && lane == 0) {
+        set_status(a.status, rc);
+        sh.fail = rc;
+      }
+    } else if (warp == 1 && it > 0) {
+      fast_deferred<M>(sh, a, f, N, it - 1, lane);
+    }
+    if (warp < 2) asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (warp == 0) {
+      if (lane == 0 && sh.fail_pending) sh.fail = sh.fail_pending;
+      if (!sh.fail) {
+        // Publish the next basis for the bin pass: P^H <- (P Q)^H from the FP32 copies.
+        for (int e = lane; e < MM; e += 32) {
+          const int i = e / M, m = e % M;  // (P Q)_{m i}
+          float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
+          sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
+        }
+        if (lane < M) {
+          sh.lam[lane] = sh.sig[b][lane];
+          sh.ilam[lane] = 1.f / sh.sig[b][lane];
+        }
+      }
+    }
+    __syncthreads();
+    if (sh.fail) break;
+    done = it + 1;
+  }
+  if (warp == 1 && done > 0 && done == a.iters) fast_deferred<M>(sh, a, f, N, done - 1, lane);
+  __syncthreads();
+
+  if (tid < MM) a.P[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
+  if (tid < M) a.lam[(size_t)f * M + tid] = sh.lam64[tid];
+  if (tid == 0) a.logdetS2[f] = sh.logdetS2;
+  if (res) {
+    for (int n = tid; n < N; n += NT) {
+      vg1[n] = vs[n];
+      vg1[dv2 + n] = vs[N + n];
+    }
+  }
+}
+
+// Posterior means in the original basis (Algorithm 1, last step): mu1 = P^-H (a .* yt),
+// a_i = v1 lam_i / (v1 lam_i + v2); mu2 = y - mu1 (y = x1 + x2, Sec. 2).
+template <int M, int ST>
+__global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
+  using E = typename Elem<ST>::T;
+  __shared__ float2 PH[M][M], PiH[M][M];
+  __shared__ float lam[M];
+  const int tid = threadIdx.x;
+  int f, N;
+  size_t yoff, xoff, v1off, v2off;
+  if (a.bins) {
+    const BinDesc d = a.bins[blockIdx.x];
+    f = d.b;
+    N = d.N;
+    yoff = (size_t)d.y_off;
+    xoff = (size_t)d.x_off;
+    v1off = (size_t)d.v1_off;
+    v2off = (size_t)d.v2_off;
+  } else {
+    f = blockIdx.x;
+    N = a.N;
+    yoff = (size_t)f * N * M;
+    xoff = yoff;
+    v1off = (size_t)f * N;
+    v2off = (size_t)a.F * N + v1off;
+  }
+  const int n = blockIdx.y * 256 + tid;
+  if (blockIdx.y * 256 >= N) return;  // whole CTA past this bin's frames
+  const size_t MM = (size_t)M * M;
+  if (tid < M * M) {
+    PH[tid / M][tid % M] = a.PH[f * MM + tid];
+    PiH[tid / M][tid % M] = a.PinvH[f * MM + tid];
+  }
+  if (tid < M) lam[tid] = a.lam[(size_t)f * M + tid];
+  __syncthreads();
+  if (n >= N) return;
+  const size_t b = xoff + (size_t)n * M;
+  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+  float2 yv[M];
+  load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + yoff + (size_t)n * M, yv);
+  const float v1 = a.v[v1off + n], v2 = a.v[v2off + n];
+  float2 mt[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 s = cmul(PH[i][0], yv[0]);
+#pragma unroll
+    for (int m = 1; m < M; ++m) s = cfma(PH[i][m], yv[m], s);
+    const float e = v1 * lam[i];
+    mt[i] = cscale(s, e / (e + v2));
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 s = cmul(PiH[i][0], mt[0]);
+#pragma unroll
+    for (int m = 1; m < M; ++m) s = cfma(PiH[i][m], mt[m], s);
+    a.x1[b + i] = s;
+    a.x2[b + i] = csub(cscale(yv[i], gi), s);
+  }
+}
+
+
+// Host-side launch of fast_em_kernel<M, ST, NT> (instantiated per translation unit).
+template <int M, int ST, int NT, bool kB>
+cudaError_t launch_fast_t(const FastEmArgs& a, cudaStream_t st) {
+  const size_t dyn = (size_t)a.res_bytes;
+  auto k = fast_em_kernel<M, ST, NT, kB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  if (dyn > 48 * 1024) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = a.bins ? a.nbins : a.F;
+  if (grid <= 0) return cudaSuccess;
+  k<<<grid, NT, dyn, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ST, int NT, bool kB>
+cudaError_t launch_fast_nt(int M, const FastEmArgs& a, cudaStream_t st) {
+  switch (M) {
+    case 1: return launch_fast_t<1, ST, NT, kB>(a, st);
+    case 2: return launch_fast_t<2, ST, NT, kB>(a, st);
+    case 3: return launch_fast_t<3, ST, NT, kB>(a, st);
+    case 4: return launch_fast_t<4, ST, NT, kB>(a, st);
+    case 5: return launch_fast_t<5, ST, NT, kB>(a, st);
+    case 6: return launch_fast_t<6, ST, NT, kB>(a, st);
+    case 7: return launch_fast_t<7, ST, NT, kB>(a, st);
+    case 8: return launch_fast_t<8, ST, NT, kB>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Defined in fca_fast_tuned.cu: batches (descriptor tables), complex64 storage, 64, 128 or
+// 256 threads per CTA.
+cudaError_t launch_fast_batch_c64(int M, const FastEmArgs& a, cudaStream_t st, int threads);
+
+}  // namespace fca

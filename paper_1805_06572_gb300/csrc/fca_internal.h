@@ -5,14 +5,37 @@
 
 namespace fca {
 
+// One frequency bin of a batch of mixtures: where its time-frequency points and source
+// powers live, and which entry of the per-bin parameter arrays it owns. A kernel given a
+// descriptor table handles bins[blockIdx] instead of bin f = blockIdx of one mixture whose
+// arrays have the [F][N][M] / [2][F][N] layouts.
+struct BinDesc {
+  long long y_off;          // element offset of the bin's first point in y (16-byte aligned)
+  long long x_off;          // element offset of the bin's first point in x1, x2
+  long long v1_off;         // offset of v_1(0, bin) in the v arrays
+  long long v2_off;         // offset of v_2(0, bin)
+  int N;                    // frames of the bin's mixture
+  int b;                    // index into the per-bin parameter arrays ([F] = bins of the class)
+};
+
+// Shared-memory bytes that keep one bin's mixture and source powers on chip for a run.
+__host__ __device__ inline size_t em_bin_smem(int M, int storage, int N) {
+  const size_t esz = storage ? 4 : 8;
+  return (((size_t)N * M * esz + 15) & ~(size_t)15) + 8 * (size_t)N;
+}
+
 // Arguments of the fused FastFCA EM kernel (one CTA per frequency bin, all iterations).
 struct FastEmArgs {
   int F, N, iters;
-  int resident;             // 1: y and v of the bin are staged in shared memory for the run
+  int res_bytes;            // dynamic shared memory of the launch; a bin whose em_bin_smem
+                            // fits is staged on chip for the run, others stream from memory
+  const BinDesc* bins;      // nullptr: one mixture, bin f = blockIdx.x
+  int nbins;                // with bins: CTAs of the launch (descriptors in bins)
   const void* y;            // complex64 or FP16 pairs, [F][N][M]
   const float* ginv;        // [F] decode scale 1/g_f (FP16 storage), else unused
   const float* vfloor;      // [F]
-  float* v;                 // [2][F][N] in/out
+  const float* v_in;        // initial v, same layout as v (may be v itself)
+  float* v;                 // [2][F][N] out (in when v_in == v)
   float* v_prev;            // [2][F][N] out: v before the last iteration
   double2* P;               // [F][M][M] in/out (FP64)
   double* lam;              // [F][M] in/out
@@ -27,13 +50,17 @@ struct FastEmArgs {
 // Arguments of the fused conventional EM kernel (one CTA per frequency bin).
 struct ConvEmArgs {
   int F, N, iters;
-  int resident;
+  int res_bytes;
+  const BinDesc* bins;
+  int nbins;
   const void* y;
   const float* ginv;
   const float* vfloor;
+  const float* v_in;
   float* v;
   float* v_prev;
-  double2* S;               // [2][F][M][M] in/out (FP64)
+  const double2* S_in;      // [2][F][M][M] initial S (may be S itself)
+  double2* S;               // [2][F][M][M] out (FP64)
   double2* S_prev;          // [2][F][M][M] out
   double* llf;              // [iters][F]
   int* status;
@@ -41,7 +68,8 @@ struct ConvEmArgs {
 
 // Posterior-mean outputs.
 struct SepFastArgs {
-  int F, N;
+  int F, N;                 // with bins: F = number of bins, N = largest N of a bin
+  const BinDesc* bins;
   const void* y;
   const float* ginv;
   const float* v;           // [2][F][N] parameters used
@@ -54,6 +82,7 @@ struct SepFastArgs {
 
 struct SepConvArgs {
   int F, N;
+  const BinDesc* bins;
   const void* y;
   const float* ginv;
   const float* v;
@@ -78,7 +107,9 @@ struct ParamArgs {
   int* status;
 };
 
-cudaError_t launch_fast_em(int M, int storage, const FastEmArgs& a, cudaStream_t st);
+// Fused EM kernels. FastFCA: threads per CTA 128 for one mixture; 64, 128 or 256 for a
+// batch (a.bins set, complex64 storage). Conventional: 128 threads per CTA.
+cudaError_t launch_fast_em(int M, int storage, const FastEmArgs& a, cudaStream_t st, int threads = 128);
 cudaError_t launch_conv_em(int M, int storage, const ConvEmArgs& a, cudaStream_t st);
 cudaError_t launch_sep_fast(int M, int storage, const SepFastArgs& a, cudaStream_t st);
 cudaError_t launch_sep_conv(int M, int storage, const SepConvArgs& a, cudaStream_t st);
@@ -90,10 +121,14 @@ cudaError_t launch_S_from_P(int M, const ParamArgs& a, cudaStream_t st);
 // (P, Lambda) -> FP32 P^H (scaled), P^-H and Lambda for the separation kernel.
 cudaError_t launch_sep_prep(int M, const ParamArgs& a, cudaStream_t st);
 
-// Positivity floor of v and conversion of the initial v.
+// Positivity floor of v and conversion of the initial v (bins: nullptr for one mixture,
+// else F = number of bins and the descriptors give each bin's N and offsets).
 cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
                            const double* v0, float* v, float* vfloor, int* status,
-                           cudaStream_t st);
+                           cudaStream_t st, const BinDesc* bins = nullptr);
+// out[mix_id[k] * iters + l] = sum of llf[l][b] over b in [b0[k], b0[k] + nb[k]), fixed order.
+cudaError_t launch_ll_ranges(int nmix, int iters, int F, const double* llf, const int* b0,
+                             const int* nb, const int* mix_id, double* out, cudaStream_t st);
 // ll[l] = sum_f llf[l][f], fixed order.
 cudaError_t launch_ll_reduce(int F, int iters, const double* llf, double* ll, cudaStream_t st);
 // ginv[f] = 1 / g[f].
@@ -107,5 +142,7 @@ void note_launches(int n);
 int em_threads(int M, int N);
 size_t em_dyn_smem(int M, int storage, int N);
 bool em_resident(int M, int storage, int N);
+// Largest dynamic shared memory a fused EM launch asks for by default (one mixture).
+constexpr size_t kResidentCap = 100 * 1024;
 
 }  // namespace fca

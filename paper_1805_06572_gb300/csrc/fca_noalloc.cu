@@ -142,10 +142,12 @@ extern "C" fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const
     a.F = F;
     a.N = N;
     a.iters = iters;
-    a.resident = fca::em_resident(M, FCA_STORE_C64, N) ? 1 : 0;
+    a.res_bytes = fca::em_resident(M, FCA_STORE_C64, N) ? (int)fca::em_dyn_smem(M, FCA_STORE_C64, N) : 0;
+    a.bins = nullptr;
     a.y = y_dev;
     a.ginv = nullptr;
     a.vfloor = vfloor;
+    a.v_in = v_dev;
     a.v = v_dev;
     a.v_prev = v_prev;
     a.P = P;

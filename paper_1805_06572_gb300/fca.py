@@ -19,6 +19,7 @@ FCA_OK = 0
 FCA_STORE_C64, FCA_STORE_F16_SCALED = 0, 1
 FCA_MEM_DEVICE, FCA_MEM_HOST = 0, 1
 FCA_SEP_ALG1, FCA_SEP_FINAL_PARAMS = 0, 1
+FCA_FORM_FAST, FCA_FORM_CONVENTIONAL = 0, 1
 STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NOMEM",
                 4: "FCA_ERR_NOT_PD", 5: "FCA_ERR_EIG_NOCONV", 6: "FCA_ERR_NONFINITE",
                 7: "FCA_ERR_TIMEOUT", 8: "FCA_ERR_STATE", 9: "FCA_ERR_SCRATCH"}
@@ -28,13 +29,20 @@ FCA_NOALLOC_SCRATCH_BYTES = 8 << 20
 EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
            "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_kernel_launches",
            "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
-           "fca_em_fast_noalloc")
+           "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
+           "fca_batch_tune", "fca_batch_shape", "fca_batch_sync_status", "fca_batch_free")
 
 
 class fca_problem(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("location", ctypes.c_int32),
                 ("y", ctypes.c_void_p), ("y_scale", ctypes.c_void_p),
+                ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p)]
+
+
+class fca_batch_problem(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("M", ctypes.c_void_p), ("F", ctypes.c_void_p),
+                ("N", ctypes.c_void_p), ("location", ctypes.c_int32), ("y", ctypes.c_void_p),
                 ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p)]
 
 
@@ -67,6 +75,17 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_status_string.restype = ctypes.c_char_p
     lib.fca_em_fast_noalloc.argtypes = [I, I, I, V, V, V, I, V, V, V, V, V]
     lib.fca_em_fast_noalloc.restype = ctypes.c_int
+    lib.fca_batch_init.argtypes = [ctypes.POINTER(fca_batch_problem), V, ctypes.POINTER(V)]
+    lib.fca_batch_load.argtypes = [V, ctypes.POINTER(fca_batch_problem), V]
+    lib.fca_batch_run.argtypes = [V, I, I, V, V, V, V, I, V]
+    lib.fca_batch_tune.argtypes = [V, I, V]
+    lib.fca_batch_shape.argtypes = [V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.fca_batch_sync_status.argtypes = [V, V]
+    lib.fca_batch_free.argtypes = [V]
+    lib.fca_batch_free.restype = None
+    for name in ("fca_batch_init", "fca_batch_load", "fca_batch_run", "fca_batch_tune",
+                 "fca_batch_shape", "fca_batch_sync_status"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.fca_version.argtypes = []
     lib.fca_version.restype = ctypes.c_char_p
     for name in ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
@@ -230,3 +249,95 @@ def run(y, v0, S0, iters: int, form: str = "fast", y_scale=None, mode: int = FCA
     v = torch.empty((2, st.F, st.N), dtype=torch.float32, device=dev)
     fca_get_params(st, v=v, stream=stream)
     return x1, x2, ll, v, st
+
+
+# ------------------------------------------------------------------------------ batches
+def batch_offsets(M, F, N):
+    """Element offsets of each mixture in the packed layouts of include/fca.h:
+    (y/x offsets in complex elements, v offsets, S offsets in complex elements) and the totals."""
+    import numpy as np
+    M, F, N = (np.asarray(a, dtype=np.int64) for a in (M, F, N))
+    fnm, fn2, fmm2 = F * N * M, 2 * F * N, 2 * F * M * M
+    off = lambda a: np.concatenate([[0], np.cumsum(a)[:-1]])  # noqa: E731
+    return (off(fnm), off(fn2), off(fmm2)), (int(fnm.sum()), int(fn2.sum()), int(fmm2.sum()))
+
+
+class Batch:
+    """Owning handle of an fca_batch."""
+
+    def __init__(self, handle: int, M, F, N):
+        self.handle = handle
+        self.M, self.F, self.N = list(M), list(F), list(N)
+        (self.x_off, self.v_off, self.S_off), (self.x_elems, self.v_elems, self.S_elems) = \
+            batch_offsets(M, F, N)
+
+    @property
+    def count(self):
+        return len(self.M)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.fca_batch_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def _batch_problem(M, F, N, y, v0, S0):
+    import numpy as np
+    Ma, Fa, Na = (np.ascontiguousarray(a, dtype=np.int32) for a in (M, F, N))
+    for t, dt in ((y, torch.complex64), (v0, torch.float64), (S0, torch.complex128)):
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError("batch inputs: y complex64, v0 float64, S0 complex128, contiguous")
+        if t.is_cuda != y.is_cuda:
+            raise ValueError("y, v0 and S0 must all be on the device or all on the host")
+    p = fca_batch_problem(count=len(Ma), M=Ma.ctypes.data, F=Fa.ctypes.data, N=Na.ctypes.data,
+                          location=FCA_MEM_DEVICE if y.is_cuda else FCA_MEM_HOST,
+                          y=y.data_ptr(), v0=v0.data_ptr(), S0=S0.data_ptr())
+    return p, (Ma, Fa, Na)
+
+
+def fca_batch_init(M, F, N, y, v0, S0, stream=None) -> Batch:
+    """y, v0, S0: flat packed tensors (complex64, float64, complex128)."""
+    p, keep = _batch_problem(M, F, N, y, v0, S0)
+    out = ctypes.c_void_p()
+    _check(lib.fca_batch_init(ctypes.byref(p), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
+           "fca_batch_init")
+    del keep
+    return Batch(out.value, M, F, N)
+
+
+def fca_batch_load(batch: Batch, y, v0, S0, stream=None):
+    p, keep = _batch_problem(batch.M, batch.F, batch.N, y, v0, S0)
+    _check(lib.fca_batch_load(ctypes.c_void_p(batch.handle), ctypes.byref(p),
+                              ctypes.c_void_p(_stream(stream))), "fca_batch_load")
+    del keep
+
+
+def fca_batch_run(batch: Batch, form: int, iters: int, x1, x2, loglik=None, v=None,
+                  use_graph: bool = False, stream=None):
+    _check(lib.fca_batch_run(ctypes.c_void_p(batch.handle), int(form), int(iters), _ptr(loglik),
+                             _ptr(x1), _ptr(x2), _ptr(v), 1 if use_graph else 0,
+                             ctypes.c_void_p(_stream(stream))), "fca_batch_run")
+
+
+def fca_batch_tune(batch: Batch, iters: int, stream=None):
+    _check(lib.fca_batch_tune(ctypes.c_void_p(batch.handle), int(iters),
+                              ctypes.c_void_p(_stream(stream))), "fca_batch_tune")
+
+
+def fca_batch_shape(batch: Batch, M: int):
+    """(bins, threads per CTA, dynamic shared memory bytes) of the channel-count group M."""
+    b, t, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.fca_batch_shape(ctypes.c_void_p(batch.handle), int(M), ctypes.byref(b),
+                               ctypes.byref(t), ctypes.byref(r)), "fca_batch_shape")
+    return b.value, t.value, r.value
+
+
+def fca_batch_sync_status(batch: Batch, stream=None) -> int:
+    return int(lib.fca_batch_sync_status(ctypes.c_void_p(batch.handle),
+                                         ctypes.c_void_p(_stream(stream))))
+
+
+def fca_batch_free(batch: Batch):
+    if batch.handle:
+        lib.fca_batch_free(ctypes.c_void_p(batch.handle))
+        batch.handle = None

@@ -60,3 +60,29 @@ def test_invalid_problems_are_rejected_on_the_host(lib):
     assert lib.fca_em_fast(None, 3, None, None) == 1
     lib.fca_free.argtypes = [ctypes.c_void_p]
     lib.fca_free(None)
+
+
+def test_invalid_batches_are_rejected_on_the_host(lib):
+    import numpy as np
+    from paper_1805_06572_gb300.fca import fca_batch_problem
+    lib.fca_batch_init.argtypes = [ctypes.POINTER(fca_batch_problem), ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+    dummy = 16
+    for Ms, Fs, Ns, kw in (([2], [3], [4], dict(count=0)), ([9], [3], [4], {}), ([0], [3], [4], {}),
+                           ([2, 2], [3, 0], [4, 4], {}), ([2], [3], [0], {}),
+                           ([2], [3], [4], dict(location=5)), ([2], [3], [4], dict(y=None)),
+                           ([2], [3], [4], dict(S0=None)), ([8], [1 << 14], [1 << 14], {})):
+        M, F, N = (np.asarray(a, dtype=np.int32) for a in (Ms, Fs, Ns))
+        args = dict(count=len(M), M=M.ctypes.data, F=F.ctypes.data, N=N.ctypes.data, location=0,
+                    y=dummy, v0=dummy, S0=dummy)
+        args.update(kw)
+        p = fca_batch_problem(**args)
+        out = ctypes.c_void_p(123)
+        assert lib.fca_batch_init(ctypes.byref(p), None, ctypes.byref(out)) == 1, (Ms, Fs, Ns, kw)
+        assert out.value is None
+    lib.fca_batch_run.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.c_void_p]
+    assert lib.fca_batch_run(None, 0, 3, None, None, None, None, 0, None) == 1
+    lib.fca_batch_free.argtypes = [ctypes.c_void_p]
+    lib.fca_batch_free(None)
