@@ -309,6 +309,140 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving workload: requests with M in {2,4,8}, N in [60, 1000], F=513, L=30, Poisson
+    arrivals at 200 requests/s, host (pinned) inputs and outputs. The server (continuous
+    admission by device memory, concurrent streams) against a plain loop that serves one
+    request at a time on one state per M; both see the same arrival times. Latency = result
+    on the host minus scheduled arrival. A saturated run (every request submitted at once)
+    gives the server's capacity."""
+    import numpy as np
+    import torch
+
+    import paper_1805_06572_gb300 as pkg
+    from synth import device as sdev
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pkg.build()
+    from paper_1805_06572_gb300 import fca
+
+    dev = torch.device("cuda", local)
+    n_req = max(200, args.steps * 100)
+    n_distinct = 100
+    c = sdev.MANY["serve"]
+    M, F, N, gaps = sdev.shapes("serve", n_req)
+    arrivals = np.cumsum(gaps)
+    L = c.iters
+    # Distinct requests (cycled): pinned host inputs and outputs.
+    pool = []
+    for k in range(n_distinct):
+        yk, vk, sk = sdev.mixture(M[k], F[k], N[k], c.delta, c.sigma, synth_seed("serve", k), dev)
+        pool.append(tuple(t.cpu().pin_memory() for t in (yk, vk, sk)) +
+                    (torch.empty(yk.shape, dtype=torch.complex64).pin_memory(),
+                     torch.empty(yk.shape, dtype=torch.complex64).pin_memory(),
+                     torch.empty(L, dtype=torch.float64).pin_memory()))
+    units = [F[k % n_distinct] * N[k % n_distinct] * L for k in range(n_req)]
+    Mk = [M[k % n_distinct] for k in range(n_req)]
+    budget = 8 << 30
+    srv = fca.fca_server_create(budget, max_inflight=16)
+
+    def serve(times):
+        launches0 = fca.fca_kernel_launches()
+        t0 = time.monotonic() + 0.05
+        tickets = []
+        for k in range(len(times)):
+            target = t0 + times[k]
+            while True:
+                d = target - time.monotonic()
+                if d <= 0:
+                    break
+                time.sleep(d if d > 2e-3 else 0)
+            y, v0, S0, x1, x2, ll = pool[k % n_distinct]
+            tickets.append(fca.fca_server_submit(srv, y, v0, S0, x1, x2, L, loglik=ll))
+        infos = [fca.fca_server_wait(srv, t) for t in tickets]
+        if any(rc != 0 for rc, _ in infos):
+            raise RuntimeError("a request failed")
+        lat = [inf["t_done"] - (t0 + times[k]) for k, (_, inf) in enumerate(infos)]
+        end = max(inf["t_done"] for _, inf in infos)
+        return lat, end - t0, fca.fca_kernel_launches() - launches0
+
+    serve(arrivals[:50] - arrivals[0])  # warm-up
+    with ClockSampler(local) as clk:
+        lat, wall, launches = serve(arrivals)
+    clocks = clk.summary()
+    st = fca.fca_server_stats(srv)
+    lat_sat, wall_sat, _ = serve(np.zeros(n_req))
+    fca.fca_server_destroy(srv)
+
+    # Plain per-request serving: one request at a time, in arrival order.
+    cap = {}
+    for k in range(n_distinct):
+        cap[M[k]] = max(cap.get(M[k], 0), N[k])
+    states = {}  # one state per M, sized for its longest request (fca_load takes shorter ones)
+    for m, n in cap.items():
+        k = next(k for k in range(n_distinct) if M[k] == m and N[k] == n)
+        y, v0, S0 = pool[k][:3]
+        states[m] = fca.fca_init(y, v0, S0)
+    stream = torch.cuda.Stream()
+    xd = {m: (torch.empty((513, cap[m], m), dtype=torch.complex64, device=dev),
+              torch.empty((513, cap[m], m), dtype=torch.complex64, device=dev)) for m in states}
+    lld = torch.empty(L, dtype=torch.float64, device=dev)
+
+    def plain(times):
+        t0 = time.monotonic() + 0.05
+        lat = []
+        for k in range(len(times)):
+            target = t0 + times[k]
+            while time.monotonic() < target:
+                pass
+            y, v0, S0, x1, x2, ll = pool[k % n_distinct]
+            m, n = y.shape[2], y.shape[1]
+            with torch.cuda.stream(stream):
+                st_m = states[m]
+                fca.fca_load(st_m, y, v0, S0, stream=stream)
+                fca.fca_em_fast(st_m, L, lld, stream=stream)
+                a = xd[m][0].view(-1)[:513 * n * m].view(513, n, m)
+                b = xd[m][1].view(-1)[:513 * n * m].view(513, n, m)
+                fca.fca_separate(st_m, a, b, fca.FCA_SEP_ALG1, stream=stream)
+                x1.copy_(a, non_blocking=True)
+                x2.copy_(b, non_blocking=True)
+                ll.copy_(lld, non_blocking=True)
+            stream.synchronize()
+            lat.append(time.monotonic() - target)
+        return lat
+
+    plain(arrivals[:50] - arrivals[0])
+    lat_plain = plain(arrivals)
+    pct = lambda a, q: float(np.percentile(np.asarray(a) * 1e3, q))  # noqa: E731
+    total = float(sum(units))
+    line = {
+        "metric": METRIC, "value": total / wall, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / n_req, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving: {n_req} requests, Poisson arrivals at {c.rate:.0f}/s, "
+                               "M uniform in {2,4,8}, N uniform in [60,1000], F=513, L=30, "
+                               f"host inputs/outputs ({n_distinct} distinct mixtures, cycled)",
+                   "form": "FastFCA", "server": {"device_bytes": budget, "max_inflight": 16},
+                   "requests_by_M": {f"M={m}": Mk.count(m) for m in sorted(set(Mk))}},
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": pct(lat, 100)},
+        "requests_per_s": n_req / wall,
+        "server_stats": {k: st[k] for k in ("max_in_flight", "bytes_peak", "completed")},
+        "saturated": {"value": total / wall_sat, "requests_per_s": n_req / wall_sat,
+                      "latency_ms": {"p50": pct(lat_sat, 50), "p99": pct(lat_sat, 99)}},
+        "plain_per_request": {"latency_ms": {"p50": pct(lat_plain, 50), "p99": pct(lat_plain, 99),
+                                             "max": pct(lat_plain, 100)}},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def synth_seed(name, k):
+    import synth
+    return synth.config_seed(name, k)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,6 +458,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import numpy as np
     import torch

@@ -37,6 +37,7 @@
 #ifndef FCA_H_
 #define FCA_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -257,6 +258,74 @@ fca_status fca_batch_sync_status(fca_batch* b, void* cuda_stream);
 
 /* Release the batch (synchronises the device first). NULL is a no-op. */
 void fca_batch_free(fca_batch* b);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving: requests of one mixture each, arriving at any time, run concurrently.
+ *
+ * A server owns one device-memory arena (allocated once, at creation), a pool of CUDA streams
+ * and a worker thread. Submitted requests wait in arrival order; the worker admits the oldest
+ * as soon as its device memory fits in the arena and a stream is free, enqueues its whole job
+ * on that stream (copies of the inputs to the device, the one-mixture EM kernels of Sec. 2 or
+ * Sec. 3 / Algorithm 1, copies of the outputs back), and retires it when the stream's event
+ * completes, returning its memory and stream to the pools. Requests admitted while others run
+ * overlap them on the GPU, and each request's results equal those it gets alone (its kernels
+ * are the one-mixture ones; bins and mixtures are independent). No device memory is allocated
+ * per request. Every wait is on the host, with a time limit where the caller gives one.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct fca_server fca_server; /* opaque, created by fca_server_create */
+
+typedef struct {
+  int64_t device_bytes;  /* size of the device-memory arena for requests in flight, >= 4096   */
+  int32_t max_inflight;  /* requests on the GPU at once (one CUDA stream each), 1..64        */
+} fca_server_config;
+
+typedef struct {
+  int32_t M, F, N;       /* 1 <= M <= 8, F >= 1, N >= 1, F N M < 2^31                           */
+  int32_t form;          /* FCA_FORM_FAST or FCA_FORM_CONVENTIONAL                               */
+  int32_t iters;         /* EM iterations L >= 0                                                 */
+  const void* y;         /* in: complex64 [F][N][M]; host (pinned for asynchronous copies) or device */
+  const double* v0;      /* in: double [2][F][N], initial v                                      */
+  const double* S0;      /* in: complex128 [2][F][M][M], initial S, Hermitian positive definite  */
+  void* x1;              /* out: complex64 [F][N][M], posterior means of Algorithm 1's output    */
+  void* x2;
+  double* loglik;        /* out: NULL or double [iters], Eq. (like) at each iteration's parameters */
+} fca_request;           /* every buffer is the caller's and must stay valid until the wait returns */
+
+typedef struct {
+  fca_status status;     /* the request's result (device-side errors included)                   */
+  double t_submit;       /* steady-clock seconds (CLOCK_MONOTONIC) of submission,                */
+  double t_admit;        /*   of admission (memory and stream granted),                          */
+  double t_done;         /*   and of completion (outputs copied back)                            */
+} fca_request_info;
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t queued, in_flight;
+  int64_t max_in_flight;               /* most requests on the GPU at once so far              */
+  uint64_t bytes_in_use, bytes_peak, bytes_budget;
+} fca_server_counters;
+
+/* Create a server on the current device: allocates the arena, the streams and the worker. */
+fca_status fca_server_create(const fca_server_config* cfg, fca_server** out);
+
+/* Device bytes one request of these shapes takes from the arena (0 for invalid shapes). */
+size_t fca_server_request_bytes(int32_t M, int32_t F, int32_t N, int32_t iters);
+
+/* Queue a request; *ticket identifies it. FCA_ERR_NOMEM if it could never fit the arena;
+ * FCA_ERR_ARG for invalid shapes or NULL buffers. Returns at once. */
+fca_status fca_server_submit(fca_server* s, const fca_request* r, uint64_t* ticket);
+
+/* Wait for a request (timeout_ms < 0: no limit) and return its status; *info (may be NULL)
+ * receives its status and times. FCA_ERR_TIMEOUT if the limit passes first (the ticket stays
+ * valid); each ticket can be waited for successfully once. */
+fca_status fca_server_wait(fca_server* s, uint64_t ticket, int64_t timeout_ms,
+                           fca_request_info* info);
+
+/* Counters and arena use. */
+fca_status fca_server_stats(fca_server* s, fca_server_counters* out);
+
+/* Finish every queued and running request, then release the server. NULL is a no-op. */
+void fca_server_destroy(fca_server* s);
 
 /* Static description of a status code. */
 const char* fca_status_string(fca_status st);

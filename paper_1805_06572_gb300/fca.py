@@ -30,7 +30,9 @@ EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_se
            "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_kernel_launches",
            "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
            "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
-           "fca_batch_tune", "fca_batch_shape", "fca_batch_sync_status", "fca_batch_free")
+           "fca_batch_tune", "fca_batch_shape", "fca_batch_sync_status", "fca_batch_free",
+           "fca_server_create", "fca_server_request_bytes", "fca_server_submit",
+           "fca_server_wait", "fca_server_stats", "fca_server_destroy")
 
 
 class fca_problem(ctypes.Structure):
@@ -44,6 +46,30 @@ class fca_batch_problem(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("M", ctypes.c_void_p), ("F", ctypes.c_void_p),
                 ("N", ctypes.c_void_p), ("location", ctypes.c_int32), ("y", ctypes.c_void_p),
                 ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p)]
+
+
+class fca_server_config(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32)]
+
+
+class fca_request(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("form", ctypes.c_int32), ("iters", ctypes.c_int32), ("y", ctypes.c_void_p),
+                ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p), ("x1", ctypes.c_void_p),
+                ("x2", ctypes.c_void_p), ("loglik", ctypes.c_void_p)]
+
+
+class fca_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class fca_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("in_flight", ctypes.c_uint64), ("max_in_flight", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64),
+                ("bytes_budget", ctypes.c_uint64)]
 
 
 class FCAError(RuntimeError):
@@ -85,6 +111,16 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_batch_free.restype = None
     for name in ("fca_batch_init", "fca_batch_load", "fca_batch_run", "fca_batch_tune",
                  "fca_batch_shape", "fca_batch_sync_status"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.fca_server_create.argtypes = [ctypes.POINTER(fca_server_config), ctypes.POINTER(V)]
+    lib.fca_server_request_bytes.argtypes = [I, I, I, I]
+    lib.fca_server_request_bytes.restype = ctypes.c_size_t
+    lib.fca_server_submit.argtypes = [V, ctypes.POINTER(fca_request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.fca_server_wait.argtypes = [V, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(fca_request_info)]
+    lib.fca_server_stats.argtypes = [V, ctypes.POINTER(fca_server_counters)]
+    lib.fca_server_destroy.argtypes = [V]
+    lib.fca_server_destroy.restype = None
+    for name in ("fca_server_create", "fca_server_submit", "fca_server_wait", "fca_server_stats"):
         getattr(lib, name).restype = ctypes.c_int
     lib.fca_version.argtypes = []
     lib.fca_version.restype = ctypes.c_char_p
@@ -341,3 +377,68 @@ def fca_batch_free(batch: Batch):
     if batch.handle:
         lib.fca_batch_free(ctypes.c_void_p(batch.handle))
         batch.handle = None
+
+
+# ------------------------------------------------------------------------------ serving
+class Server:
+    """Owning handle of an fca_server; keeps every submitted request's tensors alive until the
+    request has been waited for."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.live = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.fca_server_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def fca_server_create(device_bytes: int, max_inflight: int = 8) -> Server:
+    cfg = fca_server_config(device_bytes=int(device_bytes), max_inflight=int(max_inflight))
+    out = ctypes.c_void_p()
+    _check(lib.fca_server_create(ctypes.byref(cfg), ctypes.byref(out)), "fca_server_create")
+    return Server(out.value)
+
+
+def fca_server_request_bytes(M: int, F: int, N: int, iters: int) -> int:
+    return int(lib.fca_server_request_bytes(int(M), int(F), int(N), int(iters)))
+
+
+def fca_server_submit(srv: Server, y, v0, S0, x1, x2, iters: int, form: int = FCA_FORM_FAST,
+                      loglik=None) -> int:
+    """y complex64 [F,N,M], v0 float64 [2,F,N], S0 complex128 [2,F,M,M]; outputs x1, x2
+    complex64 [F,N,M] and loglik float64 [iters] (or None). Host tensors should be pinned."""
+    F, N, M = y.shape
+    r = fca_request(M=M, F=F, N=N, form=int(form), iters=int(iters), y=y.data_ptr(),
+                    v0=v0.data_ptr(), S0=S0.data_ptr(), x1=x1.data_ptr(), x2=x2.data_ptr(),
+                    loglik=None if loglik is None else loglik.data_ptr())
+    t = ctypes.c_uint64()
+    _check(lib.fca_server_submit(ctypes.c_void_p(srv.handle), ctypes.byref(r), ctypes.byref(t)),
+           "fca_server_submit")
+    srv.live[t.value] = (y, v0, S0, x1, x2, loglik)
+    return t.value
+
+
+def fca_server_wait(srv: Server, ticket: int, timeout_ms: int = -1):
+    """Returns (status code, {"t_submit", "t_admit", "t_done"}) (status FCA_ERR_TIMEOUT = 7 if
+    the limit passed; the ticket then stays valid)."""
+    info = fca_request_info()
+    rc = int(lib.fca_server_wait(ctypes.c_void_p(srv.handle), ctypes.c_uint64(ticket),
+                                 ctypes.c_int64(timeout_ms), ctypes.byref(info)))
+    if rc != 7:
+        srv.live.pop(ticket, None)
+    return rc, {"t_submit": info.t_submit, "t_admit": info.t_admit, "t_done": info.t_done}
+
+
+def fca_server_stats(srv: Server) -> dict:
+    c = fca_server_counters()
+    _check(lib.fca_server_stats(ctypes.c_void_p(srv.handle), ctypes.byref(c)), "fca_server_stats")
+    return {k: getattr(c, k) for k, _ in fca_server_counters._fields_}
+
+
+def fca_server_destroy(srv: Server):
+    if srv.handle:
+        lib.fca_server_destroy(ctypes.c_void_p(srv.handle))
+        srv.handle = None
+        srv.live.clear()

@@ -86,3 +86,19 @@ def test_invalid_batches_are_rejected_on_the_host(lib):
     assert lib.fca_batch_run(None, 0, 3, None, None, None, None, 0, None) == 1
     lib.fca_batch_free.argtypes = [ctypes.c_void_p]
     lib.fca_batch_free(None)
+
+
+def test_server_arguments_are_checked_on_the_host(lib):
+    from paper_1805_06572_gb300 import fca
+    out = ctypes.c_void_p(123)
+    for kw in (dict(device_bytes=0, max_inflight=4), dict(device_bytes=1 << 20, max_inflight=0),
+               dict(device_bytes=1 << 20, max_inflight=65)):
+        cfg = fca.fca_server_config(**kw)
+        assert fca.lib.fca_server_create(ctypes.byref(cfg), ctypes.byref(out)) == 1, kw
+        assert out.value is None
+    for shape in ((0, 3, 4, 1), (9, 3, 4, 1), (2, 0, 4, 1), (2, 3, 0, 1), (2, 3, 4, -1)):
+        assert fca.fca_server_request_bytes(*shape) == 0
+    assert fca.fca_server_request_bytes(8, 513, 1000, 30) > 8 * 513 * 1000 * 8 * 3
+    t = ctypes.c_uint64()
+    assert fca.lib.fca_server_submit(None, None, ctypes.byref(t)) == 1
+    fca.lib.fca_server_destroy(None)
