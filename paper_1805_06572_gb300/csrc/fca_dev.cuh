@@ -763,61 +763,136 @@ __device__ int lane_gevd(const float2 (*A)[kMaxM], const float2 (*B)[kMaxM], flo
   for (int i = 0; i < M; ++i)
 #pragma unroll
     for (int j = 0; j < M; ++j) V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-  // Cyclic Jacobi (row order), rotation as in warp_jacobi: J_pp = c, J_pq = s,
-  // J_qp = -s conj(e), J_qq = c conj(e); rows p, q of W change by J^H, columns of V by J.
+  // Cyclic Jacobi in round-robin order: each round rotates disjoint pivot pairs, whose
+  // angles depend only on their own 2 x 2 blocks, so the angle computations of a round are
+  // independent dependency chains (the rotations are then applied one after the other).
+  // Rotation as in warp_jacobi: J_pp = c, J_pq = s, J_qp = -s conj(e), J_qq = c conj(e); rows
+  // p, q of W change by J^H, columns of V by J. Once every off-diagonal entry is below 2e-4 of
+  // its eigenvalue gap, the sweeps stop with one first-order step instead (polish below).
   const float tol2 = tol * tol;
+  constexpr int n = M + (M & 1);  // even number of positions (a dummy index when M is odd)
+  constexpr int NP = n / 2;
   int sweeps = -1;
   if (M == 1) sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
     bool rotated = false, big = false;
 #pragma unroll
-    for (int p = 0; p < M - 1; ++p)
+    for (int r = 0; r < n - 1; ++r) {
+      float cs[NP], sn[NP], tt[NP], rr[NP], app[NP], aqq[NP];
+      float2 ee[NP];
+      bool act[NP];
 #pragma unroll
-      for (int q = p + 1; q < M; ++q) {
-        const float app = W[p][p].x, aqq = W[q][q].x;
+      for (int k = 0; k < NP; ++k) {
+        const int a = (k == 0) ? r : (r + k) % (n - 1);
+        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        act[k] = false;
+        if (q >= M) continue;
+        app[k] = W[p][p].x;
+        aqq[k] = W[q][q].x;
         const float2 apq = W[p][q];
         const float r2 = cabs2(apq);
-        const float den = fabsf(app * aqq);
+        const float den = fabsf(app[k] * aqq[k]);
         if (r2 > tol2 * den && r2 > 1e-36f) {
+          act[k] = true;
           rotated = true;
           big = big || (r2 > 1e-8f * den);
           float ir = rsqrtf(r2);
           ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
-          const float tau = 0.5f * (aqq - app) * ir;
+          const float tau = 0.5f * (aqq[k] - app[k]) * ir;
           const float h = fmaf(tau, tau, 1.f);
           const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
           const float g = fmaf(t, t, 1.f);
           float c = rsqrtf(g);
           c = c * fmaf(-0.5f * g * c, c, 1.5f);
-          const float sn = t * c;
-          const float2 e = cscale(apq, ir);
-          const float2 mse = cscale(e, -sn);          // -s e
-          const float2 cec = cscale(cconj(e), c);     // c conj(e)
-          const float2 msec = cscale(cconj(e), -sn);  // -s conj(e)
-          // Off-block entries (p,k), (q,k): x' = c x - s e y, y' = s x + c conj(e)^* ... (J^H rows)
-#pragma unroll
-          for (int k = 0; k < M; ++k) {
-            if (k == p || k == q) continue;
-            const float2 x = (p < k) ? W[p][k] : cconj(W[k][p]);
-            const float2 y = (q < k) ? W[q][k] : cconj(W[k][q]);
-            const float2 xn = cfma(mse, y, cscale(x, c));
-            const float2 yn = cfma(cconj(cec), y, cscale(x, sn));
-            if (p < k) W[p][k] = xn; else W[k][p] = cconj(xn);
-            if (q < k) W[q][k] = yn; else W[k][q] = cconj(yn);
-          }
-          const float rr = r2 * ir;  // |a_pq|
-          W[p][p] = make_float2(app - t * rr, 0.f);
-          W[q][q] = make_float2(aqq + t * rr, 0.f);
-          W[p][q] = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int k = 0; k < M; ++k) {  // V <- V J
-            const float2 vp = V[k][p], vq = V[k][q];
-            V[k][p] = cfma(vq, msec, cscale(vp, c));
-            V[k][q] = cfma(vq, cec, cscale(vp, sn));
-          }
+          cs[k] = c;
+          sn[k] = t * c;
+          tt[k] = t;
+          rr[k] = r2 * ir;  // |a_pq|
+          ee[k] = cscale(apq, ir);
         }
       }
-    if (!rotated || !big) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        if (!act[k]) continue;
+        const int a = (k == 0) ? r : (r + k) % (n - 1);
+        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        const float c = cs[k], sv = sn[k];
+        const float2 e = ee[k];
+        const float2 mse = cscale(e, -sv);          // -s e
+        const float2 cec = cscale(cconj(e), c);     // c conj(e)
+        const float2 msec = cscale(cconj(e), -sv);  // -s conj(e)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {  // off-block entries (p,m), (q,m): rows of J^H W
+          if (m == p || m == q) continue;
+          const float2 x = (p < m) ? W[p][m] : cconj(W[m][p]);
+          const float2 y = (q < m) ? W[q][m] : cconj(W[m][q]);
+          const float2 xn = cfma(mse, y, cscale(x, c));
+          const float2 yn = cfma(cconj(cec), y, cscale(x, sv));
+          if (p < m) W[p][m] = xn; else W[m][p] = cconj(xn);
+          if (q < m) W[q][m] = yn; else W[m][q] = cconj(yn);
+        }
+        W[p][p] = make_float2(app[k] - tt[k] * rr[k], 0.f);
+        W[q][q] = make_float2(aqq[k] + tt[k] * rr[k], 0.f);
+        W[p][q] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {  // V <- V J
+          const float2 vp = V[m][p], vq = V[m][q];
+          V[m][p] = cfma(vq, msec, cscale(vp, c));
+          V[m][q] = cfma(vq, cec, cscale(vp, sv));
+        }
+      }
+    }
+    if (!rotated || !big) {  // this sweep started within 1e-4: what is left is below rounding
+      sweeps = sweep + 1;
+      break;
+    }
+    bool small = true;
+#pragma unroll
+    for (int p = 0; p < M - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < M; ++q) {
+        const float gap = W[q][q].x - W[p][p].x;
+        small = small && (cabs2(W[p][q]) <= 4e-8f * gap * gap);
+      }
+    if (small) {
+      // First-order step: with W = D + E (E off-diagonal, |E_pq| <= 2e-4 |d_q - d_p|), the
+      // eigenvectors are I + X, X_pq = E_pq / (d_q - d_p) (X skew-Hermitian), up to O(|X|^2)
+      // = 4e-8 (below FP32 rounding), and the eigenvalues d_q + sum_p |E_pq|^2 / (d_q - d_p).
+      float2 X[M][M];
+      float d[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        X[i][i] = make_float2(0.f, 0.f);
+        d[i] = W[i][i].x;
+      }
+#pragma unroll
+      for (int p = 0; p < M - 1; ++p)
+#pragma unroll
+        for (int q = p + 1; q < M; ++q) {
+          const float ig = __fdividef(1.f, d[q] - d[p]);
+          X[p][q] = cscale(W[p][q], ig);
+          X[q][p] = make_float2(-X[p][q].x, X[p][q].y);  // -conj(X_pq)
+          const float d2 = cabs2(W[p][q]) * ig;
+          W[q][q].x += d2;
+          W[p][p].x -= d2;
+        }
+      float2 Vn[M][M];
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          float2 acc = V[i][j];
+#pragma unroll
+          for (int m = 0; m < M; ++m)
+            if (m != j) acc = cfma(V[i][m], X[m][j], acc);
+          Vn[i][j] = acc;
+        }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int j = 0; j < M; ++j) V[i][j] = Vn[i][j];
       sweeps = sweep + 1;
       break;
     }
@@ -841,6 +916,211 @@ __device__ int lane_gevd(const float2 (*A)[kMaxM], const float2 (*B)[kMaxM], flo
     }
   *ldL = ld;
   return good ? kOk : kErrNotPD;
+}
+
+// ------------------------------------------------------ register-resident solver, M <= 4
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Partner of index x in round r of the round-robin pairing of n positions (n even): position
+// n-1 stays, the others rotate. Pairs of a round are disjoint and cover every index once.
+__device__ __forceinline__ int rr_partner(int x, int r, int n) {
+  if (x == n - 1) return r;
+  if (x == r) return n - 1;
+  const int y = 2 * r - x;
+  return ((y % (n - 1)) + (n - 1)) % (n - 1);
+}
+
+// The generalised eigenproblem of lane_gevd (same contract, same outputs), with the work of
+// each step spread over the warp: lane l < M*M owns entry (l / M, l % M) of W = L^-1 A L^-H
+// and of the eigenvector matrix V, and reads the entries it needs from other lanes by
+// shuffles (no shared-memory round trips). Lane 0 factors B = L L^H and forms L^-1 (inherently
+// sequential recurrences) and writes L^-1 over B. Each Jacobi round rotates the disjoint
+// round-robin pairs at once (every lane computes the angle of its row's pair; the column's
+// comes by shuffle). Sweeps stop as in lane_gevd, or with the first-order step once every
+// off-diagonal entry is below 2e-4 of its eigenvalue gap. Called by all 32 lanes.
+template <int M>
+__device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float* sig,
+                             float2 (*Qout)[kMaxM], float2 (*Uout)[kMaxM], float* ldL, float tol,
+                             int max_sweeps, int lane) {
+  static_assert(M >= 1 && M <= 4, "one entry per lane: M*M <= 32 (and sized for M <= 4)");
+  constexpr int MM = M * M;
+  constexpr int n = M + (M & 1);
+  const bool own = lane < MM;
+  const int i = own ? lane / M : 0, j = own ? lane % M : 0;
+  // 1. Cholesky and L^-1 on lane 0.
+  int ok = 1;
+  float ld = 0.f;
+  if (lane == 0) {
+    float2 L[M][M];
+    float id[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+#pragma unroll
+      for (int r = c; r < M; ++r) {
+        float2 sv = B[r][c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) sv = csub(sv, cmulc(L[r][k], L[c][k]));
+        if (r == c) {
+          const float piv = sv.x;
+          ok = ok && (piv > 0.f) && (piv < 3.0e38f);
+          float il = rsqrtf(piv);
+          il = il * fmaf(-0.5f * piv * il, il, 1.5f);  // Newton step: 1/sqrt to rounding
+          id[c] = il;
+          L[c][c] = make_float2(piv * il, 0.f);
+        } else {
+          L[r][c] = cscale(sv, id[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      B[c][c] = make_float2(id[c], 0.f);
+      ld += 2.f * logf(id[c]);
+#pragma unroll
+      for (int r = c + 1; r < M; ++r) {
+        float2 sv = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = c; k < r; ++k) sv = cfma(L[r][k], (k == c) ? make_float2(id[c], 0.f) : B[k][c], sv);
+        B[r][c] = cscale(sv, -id[r]);
+        B[c][r] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  ld = __shfl_sync(0xffffffffu, ld, 0);
+  __syncwarp();
+  if (!ok) return kErrNotPD;
+  // 2. W = Li A Li^H: T = A Li^H (T_ij = sum_{k<=j} A_ik conj(Li_jk)), W_ij = sum_{k<=i} Li_ik T_kj.
+  float2 T = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (k <= j) T = cadd(T, cmulc(A[i][k], B[j][k]));
+  float2 W = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const float2 tk = shfl2(T, own ? k * M + j : lane);
+    if (k <= i) W = cfma(B[i][k], tk, W);
+  }
+  {  // exactly Hermitian: the lower triangle mirrors the upper one
+    const float2 wt = shfl2(W, own ? j * M + i : lane);
+    if (i > j) W = cconj(wt);
+    if (i == j) W.y = 0.f;
+  }
+  float2 V = make_float2(i == j ? 1.f : 0.f, 0.f);
+  // 3. Jacobi sweeps.
+  const float tol2 = tol * tol;
+  int sweeps = (M == 1) ? 0 : -1;
+  for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
+    int rotated = 0, big = 0;
+#pragma unroll
+    for (int r = 0; r < n - 1; ++r) {
+      const int pi = rr_partner(i, r, n), pj = rr_partner(j, r, n);
+      const int p = min(i, pi), q = max(i, pi);
+      const bool valid = own && q < M;
+      const float app = __shfl_sync(0xffffffffu, W.x, valid ? p * M + p : lane);
+      const float aqq = __shfl_sync(0xffffffffu, W.x, valid ? q * M + q : lane);
+      const float2 apq = shfl2(W, valid ? p * M + q : lane);
+      float2 Jii = make_float2(1.f, 0.f), Joi = make_float2(0.f, 0.f);  // J_{i i}, J_{i' i}
+      bool act = false;
+      if (valid) {
+        const float r2 = cabs2(apq);
+        const float den = fabsf(app * aqq);
+        if (r2 > tol2 * den && r2 > 1e-36f) {
+          act = true;
+          big |= (r2 > 1e-8f * den);
+          float ir = rsqrtf(r2);
+          ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
+          const float tau = 0.5f * (aqq - app) * ir;
+          const float h = fmaf(tau, tau, 1.f);
+          const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
+          const float g = fmaf(t, t, 1.f);
+          float c = rsqrtf(g);
+          c = c * fmaf(-0.5f * g * c, c, 1.5f);
+          const float sv = t * c;
+          const float2 e = cscale(apq, ir);
+          if (i == p) {  // J_pp = c, J_qp = -s conj(e)
+            Jii = make_float2(c, 0.f);
+            Joi = cscale(cconj(e), -sv);
+          } else {       // J_qq = c conj(e), J_pq = s
+            Jii = cscale(cconj(e), c);
+            Joi = make_float2(sv, 0.f);
+          }
+        }
+      }
+      rotated |= act;
+      // J of the column index j: computed by lane (j, 0), whose row index is j.
+      const float2 Jll = shfl2(Jii, own ? j * M : lane);
+      const float2 Jol = shfl2(Joi, own ? j * M : lane);
+      const bool ip_ok = pi < M, jp_ok = pj < M;
+      const float2 W_il2 = shfl2(W, own && jp_ok ? i * M + pj : lane);
+      const float2 W_i2l = shfl2(W, own && ip_ok ? pi * M + j : lane);
+      const float2 W_i2l2 = shfl2(W, own && ip_ok && jp_ok ? pi * M + pj : lane);
+      const float2 V_il2 = shfl2(V, own && jp_ok ? i * M + pj : lane);
+      // W' = J^H W J restricted to entry (i, j); V' = V J.
+      float2 r0 = cmul(W, Jll), r1 = cmul(W_i2l, Jll);
+      if (jp_ok) {
+        r0 = cfma(W_il2, Jol, r0);
+        r1 = cfma(W_i2l2, Jol, r1);
+      }
+      float2 Wn = ccmul(Jii, r0);
+      if (ip_ok) Wn = cadd(Wn, ccmul(Joi, r1));
+      float2 Vn = cmul(V, Jll);
+      if (jp_ok) Vn = cfma(V_il2, Jol, Vn);
+      if (i == j) Wn.y = 0.f;
+      if (act && j == pi) Wn = make_float2(0.f, 0.f);  // the pivot pair
+      W = Wn;
+      V = Vn;
+    }
+    rotated = __any_sync(0xffffffffu, rotated);
+    big = __any_sync(0xffffffffu, big);
+    if (!rotated || !big) {
+      sweeps = sweep + 1;
+      break;
+    }
+    const float di = __shfl_sync(0xffffffffu, W.x, own ? i * M + i : lane);
+    const float dj = __shfl_sync(0xffffffffu, W.x, own ? j * M + j : lane);
+    const float gap = dj - di;
+    const bool small = !own || i == j || cabs2(W) <= 4e-8f * gap * gap;
+    if (__all_sync(0xffffffffu, small)) {
+      // First-order step (as in lane_gevd): V <- V (I + X), X_ij = W_ij / (d_j - d_i);
+      // d_j += sum_p |W_pj|^2 / (d_j - d_p).
+      const float2 X = (own && i != j) ? cscale(W, __fdividef(1.f, gap)) : make_float2(0.f, 0.f);
+      float2 Vn = V;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float2 vim = shfl2(V, own ? i * M + m : lane);
+        const float2 xmj = shfl2(X, own ? m * M + j : lane);
+        Vn = cfma(vim, xmj, Vn);
+      }
+      const float e2 = W.x * X.x + W.y * X.y;  // |W_ij|^2 / (d_j - d_i)
+      float corr = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) corr += __shfl_sync(0xffffffffu, e2, own ? m * M + j : lane);
+      V = Vn;
+      if (i == j) W.x += corr;
+      sweeps = sweep + 1;
+      break;
+    }
+  }
+  if (sweeps < 0) return kErrEigNoConv;
+  // 4. Outputs: Sig, Q = Li^H V (Q_ij = sum_{k>=i} conj(Li_ki) V_kj), U = V.
+  float2 Qv = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const float2 vkj = shfl2(V, own ? k * M + j : lane);
+    if (k >= i) Qv = cadd(Qv, ccmul(B[k][i], vkj));
+  }
+  if (own) {
+    Qout[i][j] = Qv;
+    Uout[i][j] = V;
+    if (i == j) sig[i] = W.x;
+  }
+  const bool pos = !own || i != j || ((W.x > 0.f) && (W.x < 3.0e38f));
+  *ldL = ld;
+  __syncwarp();
+  return __all_sync(0xffffffffu, pos) ? kOk : kErrNotPD;
 }
 
 // ||U||_F^2 - M in FP64 (all lanes get the result).
@@ -877,6 +1157,37 @@ __device__ void warp_update_basis_q(double2 (*P)[kMaxM], const float2 (*Q)[kMaxM
   for (int t = 0; t < kPer; ++t) {
     const int e = lane + 32 * t;
     if (e < M * M) P[e / M][e % M] = out[t];
+  }
+  __syncwarp();
+}
+
+// P <- P Q in FP64 (Eq. (updatePeff)) with Q given explicitly (FP32), for 2 M^2 <= 32: lane
+// 2e + part computes the real (part 0) or imaginary (part 1) part of entry e as a pairwise sum
+// of its 2M products, which keeps the chain of dependent FP64 operations short.
+template <int M>
+__device__ void warp_update_basis_q2(double2 (*P)[kMaxM], const float2 (*Q)[kMaxM], int lane) {
+  static_assert(2 * M * M <= 32, "one real part per lane");
+  const int e = lane >> 1, part = lane & 1;
+  const int i = e / M, c = e % M;
+  double v = 0.0;
+  if (e < M * M) {
+    double t[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const double2 p = P[i][m];
+      const double qx = (double)Q[m][c].x, qy = (double)Q[m][c].y;
+      t[m] = part ? fma(p.x, qy, p.y * qx) : fma(p.x, qx, -(p.y * qy));
+    }
+#pragma unroll
+    for (int h = 1; h < M; h *= 2)
+#pragma unroll
+      for (int m = 0; m + h < M; m += 2 * h) t[m] += t[m + h];
+    v = t[0];
+  }
+  __syncwarp();
+  if (e < M * M) {
+    if (part) P[i][c].y = v;
+    else P[i][c].x = v;
   }
   __syncwarp();
 }

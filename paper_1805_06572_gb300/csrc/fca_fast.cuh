@@ -45,7 +45,7 @@ struct FastShared {
   double llt[2][2];             // sum log d, sum p/d of the iteration
   double logdetS2;
   int fail;          // read by every thread after a barrier; written only before one
-  int fail_pending;  // set by the deferred bookkeeping, folded into `fail` by warp 0
+  int fail_pending;  // set by the deferred log-likelihood, read after the iteration's barrier
   WarpLA la;
 };
 
@@ -84,16 +84,33 @@ __device__ __forceinline__ void value_entry(int v, int* g, int* i, int* k, int* 
   *k = row + 1 + pr;
 }
 
-// Deferred FP64 bookkeeping of iteration `it` (one warp): P <- P Q (Eq. (updatePeff)),
-// Lambda <- Sigma (Eq. (updateLambdaeff)), the log-likelihood of iteration it (at its own
-// parameters), log det S2 of the next iteration, and the parameters of iteration L-1.
+// Deferred FP64 bookkeeping of iteration `it`, in two parts that run on two warps at once.
+// Basis part: P <- P Q (Eq. (updatePeff)) and its FP32 copy, Lambda <- Sigma
+// (Eq. (updateLambdaeff)), and at it = L-2 the basis of iteration L-1.
 template <int M, typename Sh>
-__device__ void fast_deferred(Sh& sh, const FastEmArgs& a, int f, int N, int it, int lane) {
+__device__ void fast_deferred_basis(Sh& sh, const FastEmArgs& a, int f, int it, int lane) {
   constexpr int MM = M * M;
   const int b = it & 1;
-  warp_update_basis_q<M>(sh.P, sh.Q[b], lane);
+  if constexpr (2 * MM <= 32) {
+    warp_update_basis_q2<M>(sh.P, sh.Q[b], lane);
+  } else {
+    warp_update_basis_q<M>(sh.P, sh.Q[b], lane);
+  }
   for (int e = lane; e < MM; e += 32) sh.P32[e / M][e % M] = z2c(sh.P[e / M][e % M]);
   if (lane < M) sh.lam64[lane] = (double)sh.sig[b][lane];
+  __syncwarp();
+  if (it == a.iters - 2) {  // the parameters of iteration L-1
+    for (int e = lane; e < MM; e += 32) a.P_prev[(size_t)f * MM + e] = sh.P[e / M][e % M];
+    if (lane < M) a.lam_prev[(size_t)f * M + lane] = sh.lam64[lane];
+  }
+}
+
+// Log-likelihood part: the log-likelihood of iteration it (at its own parameters), then
+// log det S2 = -log|det P|^2 of the next basis (subtract log|det Q|^2 of the Q applied), and
+// at it = L-2 that of iteration L-1.
+template <int M, typename Sh>
+__device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int it, int lane) {
+  const int b = it & 1;
   if (lane == 0) {
     const double ll = -(double)N * M * 1.1447298858494002 - sh.llt[b][0] - sh.llt[b][1] -
                       (double)N * sh.logdetS2;
@@ -103,14 +120,10 @@ __device__ void fast_deferred(Sh& sh, const FastEmArgs& a, int f, int N, int it,
       sh.fail_pending = kErrNonFinite;
     }
   }
-  // log det S2 = -log|det P|^2 and P <- P Q: subtract log|det Q|^2 of the Q applied.
   const double ldQ = (double)sh.ldL[b] + unitarity_defect<M>(sh.U[b], lane);
-  if (lane == 0) sh.logdetS2 -= ldQ;
-  __syncwarp();
-  if (it == a.iters - 2) {  // the parameters of iteration L-1
-    for (int e = lane; e < MM; e += 32) a.P_prev[(size_t)f * MM + e] = sh.P[e / M][e % M];
-    if (lane < M) a.lam_prev[(size_t)f * M + lane] = sh.lam64[lane];
-    if (lane == 0) a.logdetS2_prev[f] = sh.logdetS2;
+  if (lane == 0) {
+    sh.logdetS2 -= ldQ;
+    if (it == a.iters - 2) a.logdetS2_prev[f] = sh.logdetS2;
   }
   __syncwarp();
 }
@@ -362,10 +375,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
       float ldL = 0.f;
       int rc;
       if constexpr (M <= 4) {
-        rc = kOk;
-        if (lane == 0) rc = lane_gevd<M>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL, 2.0e-7f, 30);
-        rc = __shfl_sync(0xffffffffu, rc, 0);
-        __syncwarp();
+        rc = warp_gevd_reg<M>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL, 2.0e-7f, 30, lane);
       } else {
         rc = warp_gevd_fast<M>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL);
       }
@@ -375,11 +385,13 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
         sh.fail = rc;
       }
     } else if (warp == 1 && it > 0) {
-      fast_deferred<M>(sh, a, f, N, it - 1, lane);
+      fast_deferred_basis<M>(sh, a, f, it - 1, lane);
+      if constexpr (NW < 3) fast_deferred_ll<M>(sh, a, f, N, it - 1, lane);
+    } else if (NW >= 3 && warp == 2 && it > 0) {
+      fast_deferred_ll<M>(sh, a, f, N, it - 1, lane);
     }
     if (warp < 2) asm volatile("bar.sync 1, 64;" ::: "memory");
     if (warp == 0) {
-      if (lane == 0 && sh.fail_pending) sh.fail = sh.fail_pending;
       if (!sh.fail) {
         // Publish the next basis for the bin pass: P^H <- (P Q)^H from the FP32 copies.
         for (int e = lane; e < MM; e += 32) {
@@ -396,10 +408,17 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
       }
     }
     __syncthreads();
-    if (sh.fail) break;
+    if (sh.fail || sh.fail_pending) break;
     done = it + 1;
   }
-  if (warp == 1 && done > 0 && done == a.iters) fast_deferred<M>(sh, a, f, N, done - 1, lane);
+  if (done > 0 && done == a.iters) {
+    if (warp == 1) {
+      fast_deferred_basis<M>(sh, a, f, done - 1, lane);
+      if constexpr (NW < 3) fast_deferred_ll<M>(sh, a, f, N, done - 1, lane);
+    } else if (NW >= 3 && warp == 2) {
+      fast_deferred_ll<M>(sh, a, f, N, done - 1, lane);
+    }
+  }
   __syncthreads();
 
   if (tid < MM) a.P[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
