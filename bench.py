@@ -438,6 +438,84 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """Precision workload: M=8, F=1025, N=4000, L=100; the mixture stored as FP16 pairs with a
+    per-frequency power scale, FP32 bin arithmetic, FP64 Gram/log-likelihood merges and basis.
+    Same step as the mid workload (load, initial GEVD, L iterations with LL, outputs)."""
+    import torch
+
+    import synth
+    import paper_1805_06572_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pkg.build()
+    from paper_1805_06572_gb300 import fca
+
+    dev = torch.device("cuda", local)
+    c, mix, v0, S0 = synth.make_config("precision")
+    y16, g, _ = synth.quantize_f16(mix["y"])
+    F, N, M, L = c.F, c.N, c.M, c.iters
+    units = F * N * L
+    yd, gd = torch.from_numpy(y16).to(dev), torch.from_numpy(g).to(dev)
+    v0d, S0d = torch.from_numpy(v0).to(dev), torch.from_numpy(S0).to(dev)
+    st = fca.fca_init(yd, v0d, S0d, y_scale=gd)
+    x1 = torch.empty((F, N, M), dtype=torch.complex64, device=dev)
+    x2 = torch.empty_like(x1)
+    ll = torch.empty(L, dtype=torch.float64, device=dev)
+
+    def step(form):
+        fca.fca_load(st, yd, v0d, S0d, y_scale=gd)
+        (fca.fca_em_fast if form == "fast" else fca.fca_em_conventional)(st, L, ll)
+        fca.fca_separate(st, x1, x2, fca.FCA_SEP_ALG1)
+
+    def timed(form, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        kms = []
+        torch.cuda.synchronize()
+        l0 = fca.fca_kernel_launches()
+        for k in range(steps):
+            evs[k][0].record()
+            step(form)
+            evs[k][1].record()
+            kms.append(fca.fca_last_em_kernel_ms(st))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs], kms, fca.fca_kernel_launches() - l0
+
+    for _ in range(args.warmup):
+        step("fast")
+    with ClockSampler(local) as clk:
+        ms, kms, launches = timed("fast", args.steps)
+    clocks = clk.summary()
+    step("conventional")
+    ms_c, kms_c, _ = timed("conventional", max(2, args.steps // 3))
+    if fca.fca_sync_status(st) != 0:
+        raise RuntimeError("device status error")
+    t, tc = statistics.mean(ms) / 1e3, statistics.mean(ms_c) / 1e3
+    kf, kc = statistics.mean(kms) / 1e3, statistics.mean(kms_c) / 1e3
+    ach = fast_flops_per_bin_iter(M) * units / kf / 1e12
+    line = {
+        "metric": METRIC, "value": units / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (y stored f16)", "data": "synthetic",
+        "config": {"workload": f"precision: M={M} F={F} N={N} L={L}, y as FP16 pairs with a "
+                               "per-frequency scale, seeded (delta=0.05, sigma=1.5)",
+                   "form": "FastFCA", "l2": "inputs (131 MB FP16 mixture + source powers) larger than L2",
+                   "step": "load + initial GEVD + L iterations with log-likelihood + posterior means"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": f"fast_em_kernel<{M},f16,128>", "kernel_ms": 1e3 * kf,
+                     "flops_per_bin_iter": fast_flops_per_bin_iter(M)},
+        "conventional": {"value": units / tc, "unit": UNIT, "ms_per_step": 1e3 * tc,
+                         "kernel_ms": 1e3 * kc, "fast_speedup": tc / t},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    fca.fca_free(st)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def synth_seed(name, k):
     import synth
     return synth.config_seed(name, k)
@@ -449,7 +527,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid", "batch", "serve"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "batch", "serve", "precision"], default="mid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -460,6 +538,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "precision":
+        return run_precision(args)
 
     import numpy as np
     import torch

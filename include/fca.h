@@ -106,6 +106,14 @@ fca_status fca_em_conventional(fca_state* s, int32_t iters, double* loglik_dev, 
  * eigenproblem of (S1, S2) (Eq. (GEVD)). loglik_dev as for fca_em_conventional. */
 fca_status fca_em_fast(fca_state* s, int32_t iters, double* loglik_dev, void* cuda_stream);
 
+/* FastFCA with the basis update of Eq. (recoverS) instead of Eq. (updatePeff), kept as a
+ * cross-check of the efficient update (Sec. 3 derives both and proves them equal): every
+ * iteration runs one FastFCA iteration, forms S_j = P^-H T_j P^-1 in the original basis
+ * (Eqs. (Sdiag), (recoverS)) and takes P, Lambda from the generalised eigenproblem of
+ * (S1, S2) afresh (Eq. (GEVD)). Same contract and outputs as fca_em_fast (equal up to
+ * rounding); three kernel launches per iteration. */
+fca_status fca_em_fast_recover(fca_state* s, int32_t iters, double* loglik_dev, void* cuda_stream);
+
 /* Posterior means (MMSE source images, Eq. (MMSE); Algorithm 1, last step) into caller-owned
  * device buffers x1_dev, x2_dev, complex64 [F][N][M].
  *   mode FCA_SEP_ALG1:         the E-step of the last iteration run, i.e. the parameters of

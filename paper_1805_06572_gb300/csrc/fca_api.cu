@@ -318,6 +318,61 @@ fca_status fca_em_fast(fca_state* s, int32_t iters, double* loglik_dev, void* st
   return FCA_OK;
 }
 
+fca_status fca_em_fast_recover(fca_state* s, int32_t iters, double* loglik_dev, void* stream) {
+  if (!s || iters < 0) return FCA_ERR_ARG;
+  if (s->failed) return FCA_ERR_STATE;
+  if (iters == 0) return FCA_OK;
+  DeviceGuard guard(s->device);
+  if (loglik_dev && !device_pointer(loglik_dev, s->device)) return FCA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  fca_status rc = ensure_llf(s, iters);
+  if (rc != FCA_OK) return rc;
+  ParamArgs pa = param_args(s);
+  pa.S = s->S;
+  pa.P = s->P;
+  pa.lam = s->lam;
+  pa.logdetS2 = s->logdetS2;
+  pa.S_out = s->S;
+  if (s->form == kFormS) {
+    FCA_CHECK_CUDA(counted(launch_gevd_from_S(s->M, pa, st)));
+    s->form = kFormP;
+  }
+  FastEmArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.F = s->F;
+  a.N = s->N;
+  a.iters = 1;
+  a.res_bytes = em_resident(s->M, s->storage, s->N) ? (int)em_dyn_smem(s->M, s->storage, s->N) : 0;
+  a.y = s->y;
+  a.ginv = s->ginv;
+  a.vfloor = s->vfloor;
+  a.v_in = s->v;
+  a.v = s->v;
+  a.v_prev = s->v_prev;
+  a.P = s->P;
+  a.lam = s->lam;
+  a.logdetS2 = s->logdetS2;
+  a.P_prev = s->P_prev;
+  a.lam_prev = s->lam_prev;
+  a.logdetS2_prev = s->logdetS2_prev;
+  a.status = s->status;
+  FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[0], st));
+  for (int l = 0; l < iters; ++l) {
+    // One iteration (E-step, M-step in the transformed basis) with the parameters of
+    // iteration l; then S_j = P^-H T_j P^-1 (Eqs. (Sdiag), (recoverS)) and (P, Lambda) from
+    // the generalised eigenproblem of (S1, S2) afresh (Eq. (GEVD)).
+    a.llf = s->llf + (size_t)l * s->F;
+    FCA_CHECK_CUDA(counted(launch_fast_em(s->M, s->storage, a, st)));
+    FCA_CHECK_CUDA(counted(launch_S_from_P(s->M, pa, st)));
+    FCA_CHECK_CUDA(counted(launch_gevd_from_S(s->M, pa, st)));
+  }
+  FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[1], st));
+  s->prev_form = kFormP;
+  s->last_iters = iters;
+  if (loglik_dev) FCA_CHECK_CUDA(counted(launch_ll_reduce(s->F, iters, s->llf, loglik_dev, st)));
+  return FCA_OK;
+}
+
 fca_status fca_em_conventional(fca_state* s, int32_t iters, double* loglik_dev, void* stream) {
   if (!s || iters < 0) return FCA_ERR_ARG;
   if (s->failed) return FCA_ERR_STATE;

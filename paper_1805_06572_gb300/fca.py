@@ -26,8 +26,9 @@ STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NO
 FCA_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 # Every entry point declared in include/fca.h.
-EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
-           "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_kernel_launches",
+EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em_fast_recover",
+           "fca_separate", "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms",
+           "fca_kernel_launches",
            "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
            "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
            "fca_batch_tune", "fca_batch_shape", "fca_batch_sync_status", "fca_batch_free",
@@ -88,6 +89,7 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_load.argtypes = [V, ctypes.POINTER(fca_problem), V]
     lib.fca_em_conventional.argtypes = [V, I, V, V]
     lib.fca_em_fast.argtypes = [V, I, V, V]
+    lib.fca_em_fast_recover.argtypes = [V, I, V, V]
     lib.fca_separate.argtypes = [V, V, V, I, V]
     lib.fca_get_params.argtypes = [V, V, V, V]
     lib.fca_loglik_bins.argtypes = [V, V, ctypes.POINTER(I), V]
@@ -124,8 +126,9 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = ctypes.c_int
     lib.fca_version.argtypes = []
     lib.fca_version.restype = ctypes.c_char_p
-    for name in ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_separate",
-                 "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms", "fca_sync_status"):
+    for name in ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em_fast_recover",
+                 "fca_separate", "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms",
+                 "fca_sync_status"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -210,6 +213,11 @@ def fca_load(state: State, y, v0, S0, y_scale=None, stream=None):
 def fca_em_fast(state: State, iters: int, loglik=None, stream=None):
     _check(lib.fca_em_fast(ctypes.c_void_p(state.handle), int(iters), _ptr(loglik),
                            ctypes.c_void_p(_stream(stream))), "fca_em_fast")
+
+
+def fca_em_fast_recover(state: State, iters: int, loglik=None, stream=None):
+    _check(lib.fca_em_fast_recover(ctypes.c_void_p(state.handle), int(iters), _ptr(loglik),
+                                   ctypes.c_void_p(_stream(stream))), "fca_em_fast_recover")
 
 
 def fca_em_conventional(state: State, iters: int, loglik=None, stream=None):
