@@ -153,12 +153,44 @@ def cpu_oracle_rate(mix, v0, S0, iters, n_bins, form="fast", min_seconds=0.0):
     reps, dt = 0, 0.0
     while reps == 0 or dt < min_seconds:
         t0 = time.perf_counter()
-        oracle.em(form, y, v0[:, fs], S0[:, fs], iters, want_mu=True)
+        res = oracle.em(form, y, v0[:, fs], S0[:, fs], iters, want_mu=True)
         dt += time.perf_counter() - t0
         reps += 1
     units = reps * len(fs) * y.shape[1] * iters
+    cpu_oracle_rate.last = (fs, res)
     return units / dt, dt, oracle.threads(), \
         f"{reps} x ({len(fs)} of {F} bins x N={y.shape[1]} x L={iters})"
+
+
+def parity_errors(gpu, ref, y):
+    """Errors of GPU outputs against the oracle (the parity tests' metrics): per entry
+    |v - v*| / v*, ||mu - mu*|| / ||y|| per time-frequency point, and the largest relative
+    log-likelihood error over the iterations. Returns {name: [median, max]}."""
+    import numpy as np
+    ev = np.abs(gpu["v"] - ref["v"]) / ref["v"]
+    yn = np.linalg.norm(y, axis=2)
+    yn = np.where(yn > 0, yn, 1.0)
+    emu = np.stack([np.linalg.norm(gpu["mu1"] - ref["mu1"], axis=2) / yn,
+                    np.linalg.norm(gpu["mu2"] - ref["mu2"], axis=2) / yn])
+    llr = ref["ll"].sum(axis=1)
+    ell = np.abs(gpu["ll"] - llr) / np.abs(llr)
+    return {"v": [float(np.median(ev)), float(ev.max())],
+            "mu": [float(np.median(emu)), float(emu.max())],
+            "ll": [float(np.median(ell)), float(ell.max())]}
+
+
+def hbm_model(M, value):
+    """Streaming byte model: a TF-bin-iteration reads y (8M bytes) and reads and writes v
+    (16 bytes) if nothing stays on chip. GB/s that the measured rate implies under it, and its
+    fraction of the measured HBM copy bandwidth."""
+    peak, src = 6800.0, "fallback"
+    try:
+        peak, src = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        pass
+    gbs = (8 * M + 16) * value / 1e9
+    return {"bytes_per_bin_iter": 8 * M + 16, "model_gbs": gbs, "peak_gbs": peak, "peak": src,
+            "frac": gbs / peak}
 
 
 def run_reference(args):
@@ -209,7 +241,7 @@ def run_batch(args):
     from paper_1805_06572_gb300 import fca
 
     dev = torch.device("cuda", local)
-    p = sdev.make_packed("batch", dev)
+    p = sdev.make_packed("batch", dev, count=args.batch_count)
     M, F, N, L = p["M"], p["F"], p["N"], p["iters"]
     units = sum(f * n for f, n in zip(F, N)) * L
     flops = sum(fast_flops_per_bin_iter(m) * f * n for m, f, n in zip(M, F, N)) * L
@@ -217,7 +249,8 @@ def run_batch(args):
     b = fca.fca_batch_init(M, F, N, p["y"], p["v0"], p["S0"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    fca.fca_batch_tune(b, L)
+    if not args.no_tune:
+        fca.fca_batch_tune(b, L)
     tune_s = time.perf_counter() - t0
     shapes = {f"M={m}": dict(zip(("bins", "threads", "smem_bytes"), fca.fca_batch_shape(b, m)))
               for m in sorted(set(M))}
@@ -281,13 +314,15 @@ def run_batch(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch: 512 mixtures, M uniform in {2,4,6}, N uniform in [200,6000], "
-                               "F=513, L=50, complex64, seeded (delta=0.05, sigma=1.5)",
+        "config": {"workload": f"batch: {len(M)} mixtures, M uniform in {{2,4,6}}, N uniform in "
+                               "[200,6000], F=513, L=50, complex64, seeded (delta=0.05, sigma=1.5)",
                    "form": "FastFCA", "mixtures_by_M": {f"M={m}": M.count(m) for m in sorted(set(M))},
                    "bin_iters_per_step": units, "l2": "inputs (26 GB) larger than L2",
                    "step": "whole batch job as one CUDA graph launch: initial GEVD + L iterations "
                            "with per-mixture log-likelihood + posterior means",
                    "tuned_shapes": shapes, "tune_s": tune_s},
+        "hbm_streaming_model": hbm_model(sum(m * f * n for m, f, n in zip(M, F, N)) /
+                                         sum(f * n for f, n in zip(F, N)), units / t),
         "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP32_PEAK_TFLOPS,
                      "traffic": None, "kernel": "fast_em_kernel<M,c64,tuned> (all groups, job time)",
@@ -529,6 +564,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["mid", "batch", "serve", "precision"], default="mid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=None,
+                    help="batch workload: the first K of its 512 mixtures (profiling runs)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batch workload: keep the default launch shapes (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -700,18 +739,34 @@ def main():
                 "ms_per_step": statistics.mean(ms_e2e),
                 "timing": "host wall clock around all steps, synchronised on both sides; "
                           "two states on two streams (copies of one step overlap another's kernels)"},
+        "hbm_streaming_model": dict(hbm_model(M, value), note="y and v stay on chip; ncu DRAM "
+                                                              "traffic per launch is in roofline.traffic"),
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s_timed_region": wall_fast,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, threads, sample = cpu_oracle_rate(mix, v0, S0, L, F, min_seconds=10.0)
+        _, ref_fast = cpu_oracle_rate.last
         rate_c, dt_c, _, sample_c = cpu_oracle_rate(mix, v0, S0, L, F, form="conventional",
                                                     min_seconds=10.0)
+        _, ref_conv = cpu_oracle_rate.last
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"FastFCA form, {sample} ({dt:.1f} s)",
                                 "conventional_value": rate_c,
                                 "conventional_sample": f"{sample_c} ({dt_c:.1f} s)"}
+        # The GPU outputs of one step of each form against those oracle runs (same inputs).
+        import numpy as np
+        parity = {}
+        for form, ref in (("fast", ref_fast), ("conventional", ref_conv)):
+            step(form)
+            v = torch.empty((2, F, N), dtype=torch.float32, device=dev)
+            fca.fca_get_params(st, v=v)
+            got = {"v": v.cpu().numpy().astype(np.float64), "mu1": x1.cpu().numpy(),
+                   "mu2": x2.cpu().numpy(), "ll": ll.cpu().numpy()}
+            parity[form] = parity_errors(got, ref, mix["y"].astype(np.complex128))
+        line["parity_vs_oracle"] = dict(parity, tolerance="median <= 1e-4, max <= 1e-3 (v, mu); "
+                                                          "ll <= 1e-6 relative")
     if rank == 0:
         print(json.dumps(line), flush=True)
     for stk in e2e_states:

@@ -70,7 +70,8 @@ def mixture(M: int, F: int, N: int, delta: float, sigma: float, seed: int, devic
     eye = torch.eye(M, dtype=torch.complex128, device=device)
     a = cn((2, F, M)).to(torch.complex128)
     R = a[..., :, None] * a[..., None, :].conj() + delta * eye
-    C = torch.linalg.cholesky(R).to(torch.complex64)                      # R = C C^H
+    # R = C C^H; the factor is tiny ([2][F][M][M]) and taken on the host.
+    C = torch.from_numpy(np.linalg.cholesky(R.cpu().numpy())).to(device=device, dtype=torch.complex64)
     v = torch.exp(sigma * torch.randn((2, F, N), generator=gen, device=device, dtype=torch.float32))
     z = cn((2, F, N, M))
     x = v.sqrt()[..., None] * torch.einsum("kfij,kfnj->kfni", C, z)       # [2][F][N][M]
