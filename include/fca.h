@@ -335,6 +335,35 @@ fca_status fca_server_stats(fca_server* s, fca_server_counters* out);
 /* Finish every queued and running request, then release the server. NULL is a no-op. */
 void fca_server_destroy(fca_server* s);
 
+/* ------------------------------------------------------------------------------------------
+ * STFT front-end: time-domain signals to the mixture y(n,f) of Sec. 2 and back.
+ *
+ * The analysis of the paper's experiments (Table 1): frames of W samples (W a power of two,
+ * 16..8192), shift H (1 <= H <= W/2), square-root periodic Hann window w[k] = sin(pi k / W),
+ * F = W/2 + 1 bins up to Nyquist (W = 1024, H = 512 gives Table 1's F = 513). Frames are
+ * centred: frame n covers samples [n H - W/2, n H + W/2), zero outside the signal, so there
+ * are N = T / H + 1 frames (fca_stft_frames). y(n,f) = sum_k w[k] x(n H - W/2 + k)
+ * exp(-2 pi i f k / W). Synthesis is weighted overlap-add with the same window,
+ * x(t) = sum_n w u_n(t) / sum_n w^2, which inverts the analysis exactly.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Frames N = T / H + 1 of a T-sample signal (0 for invalid sizes). */
+int64_t fca_stft_frames(int64_t T, int32_t W, int32_t H);
+
+/* x_dev: device float [M][T] (1 <= M <= 8) -> y_dev: device complex64 [F][N][M] (the layout of
+ * fca_problem.y). Asynchronous. */
+fca_status fca_stft(int32_t M, int64_t T, const float* x_dev, int32_t W, int32_t H, void* y_dev,
+                    void* cuda_stream);
+
+/* y_dev: device complex64 [F][N][M] with N = fca_stft_frames(T, W, H) -> x_dev: device float
+ * [M][T]; each frame is the inverse DFT of its spectrum extended by Hermitian symmetry (a real
+ * frame; the imaginary parts of the DC and Nyquist bins are dropped, as a real signal has none).
+ * frames_dev: caller-provided device scratch of N * M * W floats (the windowed frames
+ * before the overlap-add). Each output sample is gathered from its frames in a fixed order
+ * (bitwise reproducible). Asynchronous. */
+fca_status fca_istft(int32_t M, int32_t N, const void* y_dev, int32_t W, int32_t H,
+                     float* frames_dev, float* x_dev, int64_t T, void* cuda_stream);
+
 /* Static description of a status code. */
 const char* fca_status_string(fca_status st);
 

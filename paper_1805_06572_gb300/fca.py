@@ -33,7 +33,8 @@ EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em
            "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
            "fca_batch_tune", "fca_batch_shape", "fca_batch_sync_status", "fca_batch_free",
            "fca_server_create", "fca_server_request_bytes", "fca_server_submit",
-           "fca_server_wait", "fca_server_stats", "fca_server_destroy")
+           "fca_server_wait", "fca_server_stats", "fca_server_destroy", "fca_stft_frames",
+           "fca_stft", "fca_istft")
 
 
 class fca_problem(ctypes.Structure):
@@ -124,6 +125,12 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_server_destroy.restype = None
     for name in ("fca_server_create", "fca_server_submit", "fca_server_wait", "fca_server_stats"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.fca_stft_frames.argtypes = [ctypes.c_int64, I, I]
+    lib.fca_stft_frames.restype = ctypes.c_int64
+    lib.fca_stft.argtypes = [I, ctypes.c_int64, V, I, I, V, V]
+    lib.fca_stft.restype = ctypes.c_int
+    lib.fca_istft.argtypes = [I, I, V, I, I, V, V, ctypes.c_int64, V]
+    lib.fca_istft.restype = ctypes.c_int
     lib.fca_version.argtypes = []
     lib.fca_version.restype = ctypes.c_char_p
     for name in ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em_fast_recover",
@@ -450,3 +457,29 @@ def fca_server_destroy(srv: Server):
         lib.fca_server_destroy(ctypes.c_void_p(srv.handle))
         srv.handle = None
         srv.live.clear()
+
+
+# ------------------------------------------------------------------------------------ STFT
+def fca_stft_frames(T: int, W: int = 1024, H: int = 512) -> int:
+    return int(lib.fca_stft_frames(int(T), int(W), int(H)))
+
+
+def fca_stft(x, W: int = 1024, H: int = 512, stream=None):
+    """x: device float32 [M, T] -> device complex64 [F, N, M] (F = W/2 + 1)."""
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.dim() != 2:
+        raise TypeError("x must be a contiguous device float32 tensor [M, T]")
+    M, T = x.shape
+    N = fca_stft_frames(T, W, H)
+    y = torch.empty((W // 2 + 1, max(N, 1), M), dtype=torch.complex64, device=x.device)
+    _check(lib.fca_stft(M, T, _ptr(x), W, H, _ptr(y), ctypes.c_void_p(_stream(stream))), "fca_stft")
+    return y
+
+
+def fca_istft(y, T: int, W: int = 1024, H: int = 512, stream=None):
+    """y: device complex64 [F, N, M] -> device float32 [M, T]."""
+    F, N, M = y.shape
+    frames = torch.empty(N * M * W, dtype=torch.float32, device=y.device)
+    x = torch.empty((M, T), dtype=torch.float32, device=y.device)
+    _check(lib.fca_istft(M, N, _ptr(y), W, H, _ptr(frames), _ptr(x), int(T),
+                         ctypes.c_void_p(_stream(stream))), "fca_istft")
+    return x

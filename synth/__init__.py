@@ -144,3 +144,20 @@ def make_config(name: str, mixture_index: int = 0, F: int | None = None, recipe:
     mix = make_mixture(c.M, F or c.F, c.N, c.delta, c.sigma, seed)
     v0, S0 = init_params(mix["y"], seed, x=mix["x"], recipe=recipe)
     return c, mix, v0, S0
+
+
+def make_time_mixture(M: int, T: int, seed: int, taps: int = 64):
+    """Two-source M-channel time-domain mixture (input for the STFT front-end): each source is
+    white Gaussian noise under a slowly varying log-normal envelope (power changing from frame
+    to frame, as speech does), convolved per microphone with a random exponentially decaying
+    FIR of `taps` taps (a short room response). Returns (y [M][T], x [2][M][T]) float64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = np.zeros((2, M, T))
+    for k in range(2):
+        env = np.exp(0.75 * np.repeat(rng.standard_normal(T // 256 + 1), 256)[:T])
+        s = env * rng.standard_normal(T)
+        decay = np.exp(-np.arange(taps) / (taps / 4.0))
+        for m in range(M):
+            h = rng.standard_normal(taps) * decay
+            x[k, m] = np.convolve(s, h)[:T]
+    return x[0] + x[1], x
