@@ -88,6 +88,9 @@ typedef struct {
  * state; on failure *out is NULL and nothing stays allocated. */
 fca_status fca_init(const fca_problem* p, void* cuda_stream, fca_state** out);
 
+/* (fca_init and fca_load check on the device that the mixture and v0 are finite; a NaN or an
+ * infinity is reported as FCA_ERR_NONFINITE by the next fca_sync_status.) */
+
 /* Reload a state with a new mixture and initial parameters of the same M, F and storage and
  * N frames, N at most the N the state was created with (its buffers are reused; later calls
  * work on the new N). Clears a failed status. The positivity floor of v is recomputed from the new y:

@@ -5,7 +5,8 @@
 //                 parameters to the FastFCA ones);
 //   S_from_P    : S2 = P^-H P^-1, S1 = P^-H Lambda P^-1 (Eqs. (Sdiag), (recoverS));
 //   sep_prep    : FP32 P^H, P^-H and Lambda for the posterior-mean kernel;
-//   prepare     : positivity floor of v per frequency, initial v (clamped);
+//   prepare     : positivity floor of v per frequency, initial v (clamped), and a check that
+//                 the mixture and the initial v are finite;
 //   ll_reduce   : per-iteration log-likelihood summed over frequencies in a fixed order.
 // One warp handles one frequency bin; P^-1 is formed by Gauss-Jordan elimination with
 // partial pivoting in FP64 (these kernels run once per call, not once per iteration).
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
     for (int w = 0; w < 8; ++w) t += part[w];
     const double g = (ST == 1) ? (double)ginv[f] : 1.0;
     t *= g * g;
+    if (!isfinite(t)) set_status(status, kErrNonFinite);  // a NaN or infinity in the mixture
     const double fl = fmax(1e-12 * t / ((double)N * M), 1e-30);
     vf_s = (float)fl;
     vfloor[f] = (float)fl;

@@ -110,3 +110,85 @@ def test_loglik_bins_sum_to_total(fca):
     llf = fca.fca_loglik_bins(st).numpy()
     assert llf.shape == (6, 9)
     np.testing.assert_allclose(llf.sum(axis=1), ll.cpu().numpy(), rtol=1e-14)
+
+
+def _state_outputs(fca, st, F, N, M):
+    x1 = torch.empty((F, N, M), dtype=torch.complex64, device="cuda")
+    x2 = torch.empty_like(x1)
+    fca.fca_separate(st, x1, x2, fca.FCA_SEP_ALG1)
+    v = torch.empty((2, F, N), dtype=torch.float32, device="cuda")
+    S = torch.empty((2, F, M, M), dtype=torch.complex128)
+    fca.fca_get_params(st, v=v, S=S)
+    assert fca.fca_sync_status(st) == 0
+    return {"v": v.cpu().numpy().astype(np.float64), "S": S.numpy(), "mu1": x1.cpu().numpy(),
+            "mu2": x2.cpu().numpy()}
+
+
+@pytest.mark.parametrize("form", ["fast", "conventional"])
+def test_resume_in_two_calls_equals_one_call(fca, form):
+    """Checkpoint/resume: the state between calls is the EM state (v, and S or P, Lambda,
+    log det S2), so 7 + 5 iterations continue the trajectory of 12 (conventional: bitwise, the
+    FP64 S and FP32 v are exactly what the kernel keeps; FastFCA: the FP32 basis copy is
+    rebuilt from the FP64 basis at a call boundary, so within rounding), and the separation of
+    the second call is Algorithm 1's output of iteration 11."""
+    y, v0, S0 = problem(seed=31, M=4, F=6, N=200)
+    F, N, M = y.shape
+    em = fca.fca_em_fast if form == "fast" else fca.fca_em_conventional
+    a = fca.fca_init(*to_dev(y, v0, S0))
+    em(a, 12)
+    ga = _state_outputs(fca, a, F, N, M)
+    b = fca.fca_init(*to_dev(y, v0, S0))
+    em(b, 7)
+    em(b, 5)
+    gb = _state_outputs(fca, b, F, N, M)
+    if form == "conventional":
+        for k in ("v", "S", "mu1", "mu2"):
+            assert np.array_equal(ga[k], gb[k]), k
+    else:
+        rel = np.abs(ga["v"] - gb["v"]) / ga["v"]
+        assert np.median(rel) < 1e-5 and rel.max() < 1e-4
+    r = oracle.em(form, y, v0, S0, 12)
+    assert_within(errors(dict(gb, ll=np.zeros(0), llf=None), r, y, fs=np.arange(F)), "resume")
+
+
+@pytest.mark.parametrize("form", ["fast", "conventional"])
+def test_reload_with_fewer_frames(fca, form):
+    """A state sized for N = 300 frames takes a mixture of 180 frames: the same results as a
+    state made for 180 frames (bitwise)."""
+    big = problem(seed=41, M=3, F=5, N=300)
+    y, v0, S0 = problem(seed=42, M=3, F=5, N=180)
+    em = fca.fca_em_fast if form == "fast" else fca.fca_em_conventional
+    st = fca.fca_init(*to_dev(*big))
+    fca.fca_load(st, *to_dev(y, v0, S0))
+    assert st.N == 300  # the binding keeps the creation shape; the library tracks the load
+    em(st, 6)
+    x1 = torch.empty((5, 180, 3), dtype=torch.complex64, device="cuda")
+    x2 = torch.empty_like(x1)
+    fca.fca_separate(st, x1, x2)
+    assert fca.fca_sync_status(st) == 0
+    fresh = fca.fca_init(*to_dev(y, v0, S0))
+    em(fresh, 6)
+    y1 = torch.empty_like(x1)
+    y2 = torch.empty_like(x1)
+    fca.fca_separate(fresh, y1, y2)
+    assert torch.equal(x1, y1) and torch.equal(x2, y2)
+    with pytest.raises(fca.FCAError):  # more frames than the state holds
+        fca.fca_load(fresh, *to_dev(*big))
+
+
+@pytest.mark.parametrize("form", ["fast", "conventional"])
+def test_nan_in_the_mixture_is_reported_and_latched(fca, form):
+    y, v0, S0 = problem(seed=51)
+    y = y.copy()
+    y[2, 10, 1] = np.nan
+    em = fca.fca_em_fast if form == "fast" else fca.fca_em_conventional
+    st = fca.fca_init(*to_dev(y, v0, S0))
+    em(st, 3)
+    assert fca.fca_sync_status(st) == 6  # FCA_ERR_NONFINITE
+    with pytest.raises(fca.FCAError) as ei:
+        em(st, 1)
+    assert ei.value.code == 8  # FCA_ERR_STATE until the state is reloaded
+    yc, v0c, S0c = problem(seed=51)
+    fca.fca_load(st, *to_dev(yc, v0c, S0c))
+    em(st, 3)
+    assert fca.fca_sync_status(st) == 0
