@@ -635,6 +635,60 @@ __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
       result = sweep + 1;
       break;
     }
+    // First-order finish (as in warp_gevd_reg) once every off-diagonal entry is below 2e-4 of
+    // its eigenvalue gap: V <- V (I + X), X_ij = A_ij / (d_j - d_i) (skew-Hermitian, written
+    // into the free ping-pong buffer), d_j += sum_p |A_pj|^2 / (d_j - d_p).
+    // (Every gap must also stand clear of the eigenvalues' size: degenerate pairs take
+    // another sweep.)
+    int small = 1;
+    for (int e = lane; e < M * M; e += 32) {
+      const int i = e / M, j = e % M;
+      if (i != j) {
+        const float gap = Ac[j][j].x - Ac[i][i].x;
+        const float scale = fmaxf(fabsf(Ac[i][i].x), fabsf(Ac[j][j].x));
+        small &= (cabs2(Ac[i][j]) <= 4e-8f * gap * gap && fabsf(gap) > 1e-5f * scale) ? 1 : 0;
+      }
+    }
+    if (__all_sync(0xffffffffu, small)) {
+      for (int e = lane; e < M * M; e += 32) {
+        const int i = e / M, j = e % M;
+        An[i][j] = (i != j) ? cscale(Ac[i][j], __fdividef(1.f, Ac[j][j].x - Ac[i][i].x))
+                            : make_float2(0.f, 0.f);
+      }
+      __syncwarp();
+      float2 nv[kPer];
+      float corr[kPer];
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = lane + 32 * t;
+        corr[t] = 0.f;
+        if (e < M * M) {
+          const int i = e / M, j = e % M;
+          float2 acc = Vc[i][j];
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc = cfma(Vc[i][m], An[m][j], acc);
+          nv[t] = acc;
+          if (i == j) {
+#pragma unroll
+            for (int p2 = 0; p2 < M; ++p2)
+              corr[t] = fmaf(Ac[p2][j].x, An[p2][j].x, fmaf(Ac[p2][j].y, An[p2][j].y, corr[t]));
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int e = lane + 32 * t;
+        if (e < M * M) {
+          const int i = e / M, j = e % M;
+          Vc[i][j] = nv[t];
+          if (i == j) Ac[i][i].x += corr[t];
+        }
+      }
+      __syncwarp();
+      result = sweep + 1;
+      break;
+    }
   }
   if (Ac != la.A) {  // bring the result back to la.A / la.V
     for (int e = lane; e < M * M; e += 32) {
@@ -1082,7 +1136,10 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
     const float di = __shfl_sync(0xffffffffu, W.x, own ? i * M + i : lane);
     const float dj = __shfl_sync(0xffffffffu, W.x, own ? j * M + j : lane);
     const float gap = dj - di;
-    const bool small = !own || i == j || cabs2(W) <= 4e-8f * gap * gap;
+    // (Every gap must also stand clear of the eigenvalues' size: degenerate pairs take
+    // another sweep.)
+    const bool small = !own || i == j ||
+                       (cabs2(W) <= 4e-8f * gap * gap && fabsf(gap) > 1e-5f * fmaxf(fabsf(di), fabsf(dj)));
     if (__all_sync(0xffffffffu, small)) {
       // First-order step (as in lane_gevd): V <- V (I + X), X_ij = W_ij / (d_j - d_i);
       // d_j += sum_p |W_pj|^2 / (d_j - d_p).
