@@ -158,6 +158,26 @@ __device__ __forceinline__ void warp_transpose_reduce(float* acc, int lane) {
   }
 }
 
+// As warp_transpose_reduce but over the lanes of equal parity only (levels xor 16, 8, 4, 2):
+// afterwards lane l holds, in acc[0..VP/16), the sums over the 16 lanes of parity l & 1 of
+// values [(l >> 1) VP/16, ((l >> 1) + 1) VP/16).
+template <int VP>
+__device__ __forceinline__ void warp_transpose_reduce_parity(float* acc, int lane) {
+  static_assert(VP % 32 == 0, "VP must be a multiple of 32");
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int o = 16 >> r;
+    const int h = VP >> (r + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      float send = up ? acc[j] : acc[j + h];
+      float keep = up ? acc[j + h] : acc[j];
+      acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
 // Shape of the per-lane partial-sum vector for V values: VT values go through the transpose
 // reduction (a multiple of 32) and the last VR (at most 4) through plain butterflies, which is
 // cheaper than padding a short tail to 32.
@@ -188,6 +208,36 @@ __device__ __forceinline__ void warp_reduce_store(float* acc, int lane, float* o
 #pragma unroll
     for (int j = 0; j < RS::KP; ++j)
       if (RS::KP * lane + j < V) out[RS::KP * lane + j] = acc[j];
+  }
+}
+
+// Lane pairs: lanes of parity q hold one M x M Gram (MM values, Gram q) and the two
+// log-likelihood sums (only parity 0 adds to them) in acc[0..MM+2). Reduce over the lanes of
+// each parity and store the warp's sums in the usual layout out[0..2MM+2): Gram 1, Gram 2,
+// then the two log-likelihood sums.
+template <int MM>
+__device__ __forceinline__ void warp_reduce_store_pairs(float* acc, int lane, float* out) {
+  constexpr int VP = MM + 2;
+  using RS = RedShape<VP>;
+  const int q = lane & 1;
+  auto put = [&](int v, float x) {
+    if (v < MM) out[q * MM + v] = x;
+    else if (v < VP && q == 0) out[2 * MM + (v - MM)] = x;
+  };
+  if constexpr (RS::VR > 0) {
+#pragma unroll
+    for (int j = 0; j < RS::VR; ++j) {
+      float x = acc[RS::VT + j];
+#pragma unroll
+      for (int o = 16; o >= 2; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane < 2) put(RS::VT + j, x);
+    }
+  }
+  if constexpr (RS::VT > 0) {
+    warp_transpose_reduce_parity<RS::VT>(acc, lane);
+    constexpr int KP = RS::VT / 16;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) put((lane >> 1) * KP + j, acc[j]);
   }
 }
 

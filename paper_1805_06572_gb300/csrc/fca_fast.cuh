@@ -139,6 +139,10 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
   constexpr int V = Sh::V;
   constexpr int MM = M * M;
   constexpr bool kHoist = (M <= 4);
+  // M = 8: a lane pair shares each time-frequency point and lane parity q accumulates Gram q
+  // only (two 8 x 8 Grams per thread, 130 partial sums, do not fit in registers; at M = 7 they
+  // still do, and one lane per point is faster).
+  constexpr bool kPair = (M >= 8);
   __shared__ Sh sh;
   extern __shared__ __align__(16) unsigned char dyn[];
 
@@ -233,8 +237,9 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
   for (int it = 0; it < a.iters; ++it) {
     const bool last = (it == a.iters - 1);
     const int b = it & 1;
-    using RS = RedShape<V>;
+    using RS = RedShape<kPair ? MM + 2 : V>;
     float acc[RS::NA];
+    const int q = kPair ? (lane & 1) : 0;
 #pragma unroll
     for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
     float2 ph[kHoist ? M : 1][kHoist ? M : 1];
@@ -251,11 +256,11 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
       ilamr[i] = sh.ilam[i];
     }
 
-    for (int n = tid; n < N; n += NT) {
+    for (int n = kPair ? (tid >> 1) : tid; n < N; n += kPair ? NT / 2 : NT) {
       float2 yv[M];
       load_bin<M, ST>(ysrc + (size_t)n * M, yv);
       const float v1 = v1p[n], v2 = v2p[n];
-      if (last) {
+      if (last && q == 0) {
         vg1[d_prev + n] = v1;
         vg1[d_prev + dv2 + n] = v2;
       }
@@ -299,37 +304,67 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
       }
       const float v1n = fmaxf((v1 * (1.f / M)) * fmaf(v1, sA, v2 * sB), vf);
       const float v2n = fmaxf((v2 * (1.f / M)) * fmaf(v2, sC, v1 * sD), vf);
-      v1p[n] = v1n;
-      v2p[n] = v2n;
+      if (q == 0) {
+        v1p[n] = v1n;
+        v2p[n] = v2n;
+      }
       const float rs1 = rsqrtf(v1n), rs2 = rsqrtf(v2n);
       const float a1 = v1 * rs1, a2 = v2 * rs2;
       const float v12 = v1 * v2;
       const float k1 = v12 * (rs1 * rs1), k2 = v12 * (rs2 * rs2);
-      float s1[M], s2[M];
+      if constexpr (kPair) {
+        // Gram q of this lane: weights s_q,i (s_1,i = a1 t_i, s_2,i = a2 r_i) and k_q.
+        const float kq = q ? k2 : k1;
+        const float aq = q ? a2 : a1;
+        float sq[M];
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        s1[i] = a1 * t[i];
-        s2[i] = a2 * r[i];
-        acc[i] = fmaf(s1[i] * s1[i], pp[i], fmaf(k1, t[i], acc[i]));
-        acc[MM + i] = fmaf(s2[i] * s2[i], pp[i], fmaf(k2, t[i], acc[MM + i]));
-      }
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-#pragma unroll
-        for (int k = i + 1; k < M; ++k) {
-          const int o = M + 2 * pair_index(M, i, k);
-          const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
-          const float w1 = s1[i] * s1[k], w2 = s2[i] * s2[k];
-          acc[o] = fmaf(w1, z.x, acc[o]);
-          acc[o + 1] = fmaf(w1, z.y, acc[o + 1]);
-          acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
-          acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
+        for (int i = 0; i < M; ++i) {
+          sq[i] = aq * (q ? r[i] : t[i]);
+          acc[i] = fmaf(sq[i] * sq[i], pp[i], fmaf(kq, t[i], acc[i]));
         }
-      acc[2 * MM] += lp.log_fast();
-      acc[2 * MM + 1] += ql;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+          for (int k = i + 1; k < M; ++k) {
+            const int o = M + 2 * pair_index(M, i, k);
+            const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
+            const float w = sq[i] * sq[k];
+            acc[o] = fmaf(w, z.x, acc[o]);
+            acc[o + 1] = fmaf(w, z.y, acc[o + 1]);
+          }
+        acc[MM] += q ? 0.f : lp.log_fast();
+        acc[MM + 1] += q ? 0.f : ql;
+      } else {
+        float s1[M], s2[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          s1[i] = a1 * t[i];
+          s2[i] = a2 * r[i];
+          acc[i] = fmaf(s1[i] * s1[i], pp[i], fmaf(k1, t[i], acc[i]));
+          acc[MM + i] = fmaf(s2[i] * s2[i], pp[i], fmaf(k2, t[i], acc[MM + i]));
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+          for (int k = i + 1; k < M; ++k) {
+            const int o = M + 2 * pair_index(M, i, k);
+            const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
+            const float w1 = s1[i] * s1[k], w2 = s2[i] * s2[k];
+            acc[o] = fmaf(w1, z.x, acc[o]);
+            acc[o + 1] = fmaf(w1, z.y, acc[o + 1]);
+            acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
+            acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
+          }
+        acc[2 * MM] += lp.log_fast();
+        acc[2 * MM + 1] += ql;
+      }
     }
 
-    warp_reduce_store<V>(acc, lane, sh.red[warp]);
+    if constexpr (kPair) {
+      warp_reduce_store_pairs<MM>(acc, lane, sh.red[warp]);
+    } else {
+      warp_reduce_store<V>(acc, lane, sh.red[warp]);
+    }
     __syncthreads();
     // Merge the warp partials in a fixed order: Gram entries in FP32 (they feed the FP32
     // eigensolver), the two log-likelihood sums with a compensated two-float sum kept in
