@@ -456,7 +456,7 @@ static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  if (dyn > 48 * 1024) {
+  if (dyn > 0) {  // the default limit (48 KB) covers static and dynamic shared memory together
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }

@@ -536,7 +536,7 @@ cudaError_t launch_fast_t(const FastEmArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  if (dyn > 48 * 1024) {
+  if (dyn > 0) {  // the default limit (48 KB) covers static and dynamic shared memory together
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }

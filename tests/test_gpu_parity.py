@@ -184,3 +184,15 @@ def test_posterior_means_add_up_to_mixture():
         g = gpu_run(form, y, v0, S0, 5)
         err = np.linalg.norm(g["mu1"] + g["mu2"] - y, axis=2) / np.linalg.norm(y, axis=2)
         assert err.max() < 2e-6, form
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_resident_bin_just_under_48k_of_dynamic_shared_memory(form):
+    """M=5, N=1000: the bin's mixture and source powers take 48,000 bytes of dynamic shared
+    memory, which with the kernel's static shared memory exceeds the default 48 KB per CTA;
+    the launch must opt in to more."""
+    y, v0, S0 = rand_problem(17, 5, 4, 1000)
+    g = gpu_run(form, y, v0, S0, 4)
+    assert g["status"] == 0
+    r = oracle.em(form, y, v0, S0, 4)
+    assert_within(errors(g, r, y), form)
