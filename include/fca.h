@@ -253,8 +253,11 @@ fca_status fca_batch_run(fca_batch* b, int32_t form, int32_t iters, double* logl
 /* Autotune the FastFCA launch shape of every channel-count group: threads per CTA (64, 128,
  * 256) and how much shared memory a CTA may take to keep its bin's mixture and source powers
  * on chip (bins that do not fit stream them from memory every iteration). Each candidate runs
- * min(iters, 3) iterations on a sample of the group's bins spanning its range of lengths;
- * the fastest is kept for later runs. Synchronises the stream. Overwrites the EM state (not the
+ * min(iters, 4) iterations on a sample of the group's bins (at most 8192) spanning its range
+ * of lengths, four times in turn with the others after a warm-up; the one with the best time
+ * is kept. As the groups of a job share the GPU, the tuned set is then checked against the
+ * default shapes and against all bins streaming, with whole EM passes of all groups at once,
+ * and the fastest set is kept for later runs. Synchronises the stream. Overwrites the EM state (not the
  * loaded inputs), so run it before fca_batch_run, not between a run and the use of its outputs. */
 fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* cuda_stream);
 
@@ -262,6 +265,11 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* cuda_stream);
  * dynamic shared memory per CTA. FCA_ERR_ARG if no mixture has M channels. */
 fca_status fca_batch_shape(const fca_batch* b, int32_t M, int32_t* bins, int32_t* threads,
                            int32_t* res_bytes);
+
+/* Set the launch shape of the channel-count group M (e.g. to reuse shapes tuned earlier):
+ * threads per CTA 64, 128 or 256, and res_bytes (0..200 KB) of dynamic shared memory per CTA,
+ * bins needing at most that staying on chip. FCA_ERR_ARG if no mixture has M channels. */
+fca_status fca_batch_set_shape(fca_batch* b, int32_t M, int32_t threads, int32_t res_bytes);
 
 /* Synchronise the stream and return the first device-side error of this batch. After an
  * error every run returns FCA_ERR_STATE until fca_batch_load. */

@@ -555,7 +555,7 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* stream) {
   if (b->failed || !b->loaded) return FCA_ERR_STATE;
   DeviceGuard guard(b->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const int it = std::max(1, std::min((int)iters, 3));
+  const int it = std::max(1, std::min((int)iters, 4));
   cudaEvent_t t0, t1;
   B_CHECK(cudaEventCreate(&t0));
   B_CHECK(cudaEventCreate(&t1));
@@ -565,9 +565,9 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* stream) {
       rc = FCA_ERR_NOMEM;
       break;
     }
-    // Sample: every k-th bin of the longest-first order (at most 4096 bins), so the sample
+    // Sample: every k-th bin of the longest-first order (at most 8192 bins), so the sample
     // spans the class's range of lengths.
-    const int k = std::max(1, (c.nbins + 4095) / 4096);
+    const int k = std::max(1, (c.nbins + 8191) / 8192);
     std::vector<BinDesc> smp;
     for (int i = 0; i < c.nbins; i += k) smp.push_back(c.host_bins[i]);
     if (c.sample) cudaFree(c.sample);
@@ -589,8 +589,12 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* stream) {
       break;
     }
     note_launches(1);
-    int best_t = c.threads, best_r = c.res_bytes;
-    float best_ms = 3.0e38f;
+    // Candidates: threads per CTA x the largest on-chip need admitted under each cap.
+    struct Cand {
+      int nt, rb;
+      float best;
+    };
+    std::vector<Cand> cands;
     const int threads[] = {64, 128, 256};
     const size_t caps[] = {0, 48 * 1024, 100 * 1024, 200 * 1024};
     for (int nt : threads) {
@@ -599,36 +603,91 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* stream) {
         const int rb = resident_bytes(c, cap);
         if (std::find(tried.begin(), tried.end(), rb) != tried.end()) continue;
         tried.push_back(rb);
+        cands.push_back({nt, rb, 3.0e38f});
+      }
+    }
+    // One warm-up round, then four timed rounds over all candidates in turn (a drift of the
+    // clocks during tuning then affects every candidate alike); each keeps its best time.
+    for (int rep = 0; rep < 5; ++rep) {
+      for (Cand& cd : cands) {
+        if (cd.best < 0.f) continue;  // failed to launch
         FastEmArgs a = fast_args(b, c, it, c.sample, c.nsample);
-        a.res_bytes = rb;
-        float ms_min = 3.0e38f;
-        for (int rep = 0; rep < 3; ++rep) {
-          cudaEventRecord(t0, st);
-          const cudaError_t e = launch_fast_em(c.M, 0, a, st, nt);
-          cudaEventRecord(t1, st);
-          if (e != cudaSuccess) {
-            cudaGetLastError();
-            ms_min = 3.0e38f;
-            break;
-          }
-          note_launches(1);
-          float ms = 0.f;
-          if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
-            ms_min = 3.0e38f;
-            break;
-          }
-          if (rep > 0) ms_min = std::min(ms_min, ms);  // the first run is a warm-up
+        a.res_bytes = cd.rb;
+        cudaEventRecord(t0, st);
+        const cudaError_t e = launch_fast_em(c.M, 0, a, st, cd.nt);
+        cudaEventRecord(t1, st);
+        float ms = 0.f;
+        if (e != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+          cudaGetLastError();
+          cd.best = -1.f;
+          continue;
         }
-        if (ms_min < best_ms) {
-          best_ms = ms_min;
-          best_t = nt;
-          best_r = rb;
-        }
+        note_launches(1);
+        if (rep > 0) cd.best = std::min(cd.best, ms);
+      }
+    }
+    int best_t = c.threads, best_r = c.res_bytes;
+    float best_ms = 3.0e38f;
+    for (const Cand& cd : cands) {
+      if (cd.best >= 0.f && cd.best < best_ms) {
+        best_ms = cd.best;
+        best_t = cd.nt;
+        best_r = cd.rb;
       }
     }
     c.threads = best_t;
     c.res_bytes = best_r;
     c.tuned = 1;
+  }
+  // The groups of a job run at the same time and share the SMs, so the per-group choices are
+  // checked together: the tuned shapes, the default shapes (128 threads, bins of up to 100 KB
+  // on chip) and the tuned thread counts with every bin streaming each run all groups'
+  // EM kernels at once (fork/join over the group streams); the fastest set is kept.
+  if (rc == FCA_OK && b->cls.size() > 1) {
+    struct Shape {
+      int nt, rb;
+    };
+    std::vector<std::vector<Shape>> sets(3);
+    for (BatchClass& c : b->cls) {
+      sets[0].push_back({c.threads, c.res_bytes});
+      sets[1].push_back({128, resident_bytes(c, kResidentCap)});
+      sets[2].push_back({c.threads, 0});
+    }
+    float best = 3.0e38f;
+    int best_set = 0;
+    for (int rep = 0; rep < 3 && rc == FCA_OK; ++rep) {
+      for (int si = 0; si < 3; ++si) {
+        cudaEventRecord(t0, st);
+        cudaEventRecord(b->fork, st);
+        bool ok = true;
+        for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+          BatchClass& c = b->cls[ci];
+          cudaStreamWaitEvent(c.stream, b->fork, 0);
+          FastEmArgs a = fast_args(b, c, it, c.bins, c.nbins);
+          a.res_bytes = sets[si][ci].rb;
+          if (launch_fast_em(c.M, 0, a, c.stream, sets[si][ci].nt) != cudaSuccess) ok = false;
+          else note_launches(1);
+          cudaEventRecord(c.done, c.stream);
+          cudaStreamWaitEvent(st, c.done, 0);
+        }
+        cudaEventRecord(t1, st);
+        float ms = 0.f;
+        if (!ok || cudaEventSynchronize(t1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        if (rep > 0 && ms < best) {  // the first round is a warm-up
+          best = ms;
+          best_set = si;
+        }
+      }
+    }
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+      b->cls[ci].threads = sets[best_set][ci].nt;
+      b->cls[ci].res_bytes = sets[best_set][ci].rb;
+    }
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
@@ -644,6 +703,20 @@ fca_status fca_batch_shape(const fca_batch* b, int32_t M, int32_t* bins, int32_t
     if (bins) *bins = c.nbins;
     if (threads) *threads = c.threads;
     if (res_bytes) *res_bytes = c.res_bytes;
+    return FCA_OK;
+  }
+  return FCA_ERR_ARG;
+}
+
+fca_status fca_batch_set_shape(fca_batch* b, int32_t M, int32_t threads, int32_t res_bytes) {
+  if (!b || (threads != 64 && threads != 128 && threads != 256) || res_bytes < 0 ||
+      res_bytes > 200 * 1024)
+    return FCA_ERR_ARG;
+  for (BatchClass& c : b->cls) {
+    if (c.M != M) continue;
+    c.threads = threads;
+    c.res_bytes = res_bytes;
+    drop_graph(b);
     return FCA_OK;
   }
   return FCA_ERR_ARG;

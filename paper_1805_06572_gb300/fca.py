@@ -31,7 +31,8 @@ EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em
            "fca_kernel_launches",
            "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
            "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
-           "fca_batch_tune", "fca_batch_shape", "fca_batch_sync_status", "fca_batch_free",
+           "fca_batch_tune", "fca_batch_shape", "fca_batch_set_shape", "fca_batch_sync_status",
+           "fca_batch_free",
            "fca_server_create", "fca_server_request_bytes", "fca_server_submit",
            "fca_server_wait", "fca_server_stats", "fca_server_destroy", "fca_stft_frames",
            "fca_stft", "fca_istft")
@@ -109,6 +110,8 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_batch_run.argtypes = [V, I, I, V, V, V, V, I, V]
     lib.fca_batch_tune.argtypes = [V, I, V]
     lib.fca_batch_shape.argtypes = [V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.fca_batch_set_shape.argtypes = [V, I, I, I]
+    lib.fca_batch_set_shape.restype = ctypes.c_int
     lib.fca_batch_sync_status.argtypes = [V, V]
     lib.fca_batch_free.argtypes = [V]
     lib.fca_batch_free.restype = None
@@ -381,6 +384,11 @@ def fca_batch_shape(batch: Batch, M: int):
     _check(lib.fca_batch_shape(ctypes.c_void_p(batch.handle), int(M), ctypes.byref(b),
                                ctypes.byref(t), ctypes.byref(r)), "fca_batch_shape")
     return b.value, t.value, r.value
+
+
+def fca_batch_set_shape(batch: Batch, M: int, threads: int, res_bytes: int):
+    _check(lib.fca_batch_set_shape(ctypes.c_void_p(batch.handle), int(M), int(threads),
+                                   int(res_bytes)), "fca_batch_set_shape")
 
 
 def fca_batch_sync_status(batch: Batch, stream=None) -> int:

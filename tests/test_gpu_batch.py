@@ -157,3 +157,28 @@ def test_host_inputs_and_reload(env):
     for p, q in zip(a, c):
         assert np.array_equal(p, q)
     fca.fca_batch_free(b)
+
+
+def test_set_shape_reuses_shapes_and_keeps_parity(env):
+    """Shapes set by hand (64 threads, nothing on chip; 256 threads, everything that fits on
+    chip) give results within the parity tolerances of the oracle."""
+    fca, torch, mixes = env
+    sub = mixes[:6]
+    b = fca.fca_batch_init([m[0].shape[2] for m in sub], [m[0].shape[0] for m in sub],
+                           [m[0].shape[1] for m in sub], *_pack(torch, sub))
+    for threads, res in ((64, 0), (256, 200 * 1024)):
+        for M in sorted(set(b.M)):
+            fca.fca_batch_set_shape(b, M, threads, res)
+            assert fca.fca_batch_shape(b, M)[1:] == (threads, res)
+        out = _run(fca, torch, b, fca.FCA_FORM_FAST, 6, graph=True)
+        for k, (y, v0, S0) in enumerate(sub):
+            got = _unpack(b, k, *out, 6)
+            r = oracle.em("fast", y, v0, S0, 6)
+            got["S"] = r["S"]
+            assert_within(errors(got, r, y), f"mixture {k} threads {threads}")
+    absent = next(m for m in range(1, 9) if m not in b.M)
+    with pytest.raises(fca.FCAError):
+        fca.fca_batch_set_shape(b, absent, 128, 0)
+    with pytest.raises(fca.FCAError):
+        fca.fca_batch_set_shape(b, b.M[0], 96, 0)
+    fca.fca_batch_free(b)
