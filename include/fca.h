@@ -89,7 +89,10 @@ typedef struct {
 fca_status fca_init(const fca_problem* p, void* cuda_stream, fca_state** out);
 
 /* (fca_init and fca_load check on the device that the mixture and v0 are finite; a NaN or an
- * infinity is reported as FCA_ERR_NONFINITE by the next fca_sync_status.) */
+ * infinity is reported as FCA_ERR_NONFINITE by the next fca_sync_status. They also solve the
+ * generalised eigenproblem of S0 (Eq. (GEVD)) in the same pass, so an S0_2 that is not
+ * positive definite is reported as FCA_ERR_NOT_PD whichever EM form runs next. Device inputs
+ * are read once, by that pass, which copies y and S0 into the state.) */
 
 /* Reload a state with a new mixture and initial parameters of the same M, F and storage and
  * N frames, N at most the N the state was created with (its buffers are reused; later calls

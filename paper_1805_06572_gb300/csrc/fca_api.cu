@@ -14,7 +14,9 @@ using namespace fca;
 
 namespace {
 
-enum { kFormS = 0, kFormP = 1 };
+// kFormS: S holds the parameters; kFormP: (P, Lambda) do; kFormSP: both (S0 and its
+// generalised eigenproblem, as left by a load).
+enum { kFormS = 0, kFormP = 1, kFormSP = 2 };
 
 std::atomic<uint64_t> g_launches{0};
 
@@ -105,6 +107,8 @@ bool device_pointer(const void* ptr, int device) {
   return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
 }
 
+bool aligned(const void* ptr, size_t a) { return reinterpret_cast<uintptr_t>(ptr) % a == 0; }
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
@@ -180,22 +184,43 @@ fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
   s->N = p->N;
   s->FN = (size_t)s->F * s->N;
   const size_t ybytes = s->FN * s->M * (s->storage ? 4 : 8);
-  FCA_CHECK_CUDA(cudaMemcpyAsync(s->y, p->y, ybytes, cudaMemcpyDefault, st));
+  // Device inputs: the prepare pass copies y and S0 into the state as it reads them. Host
+  // inputs: copied up first, then read in place.
+  // (Element-misaligned device inputs take the copy route too.)
+  const bool on_dev = p->location == FCA_MEM_DEVICE;
+  const bool y_direct = on_dev && aligned(p->y, s->storage ? 4 : 8);
+  const bool S_direct = on_dev && aligned(p->S0, 16);
+  PrepareExtra ex;
+  std::memset(&ex, 0, sizeof(ex));
+  ex.P = s->P;
+  ex.lam = s->lam;
+  ex.logdetS2 = s->logdetS2;
+  if (y_direct) {
+    ex.y_copy = s->y;
+  } else {
+    FCA_CHECK_CUDA(cudaMemcpyAsync(s->y, p->y, ybytes, cudaMemcpyDefault, st));
+  }
+  if (S_direct) {
+    ex.S = static_cast<const double2*>(static_cast<const void*>(p->S0));
+    ex.S_copy = s->S;
+  } else {
+    FCA_CHECK_CUDA(cudaMemcpyAsync(s->S, p->S0, 2 * s->F * s->MM * sizeof(double2), cudaMemcpyDefault, st));
+    ex.S = s->S;
+  }
   if (s->storage == FCA_STORE_F16_SCALED) {
     FCA_CHECK_CUDA(cudaMemcpyAsync(s->g, p->y_scale, s->F * sizeof(float), cudaMemcpyDefault, st));
     FCA_CHECK_CUDA(counted(launch_invert_scale(s->F, s->g, s->ginv, st)));
   }
-  FCA_CHECK_CUDA(cudaMemcpyAsync(s->S, p->S0, 2 * s->F * s->MM * sizeof(double2), cudaMemcpyDefault, st));
   const double* v0 = p->v0;
-  if (p->location == FCA_MEM_HOST) {
+  if (!on_dev || !aligned(p->v0, 8)) {
     if (!s->v0_stage) FCA_CHECK_CUDA(dalloc(&s->v0_stage, 2 * (size_t)s->F * s->N_cap));
     FCA_CHECK_CUDA(cudaMemcpyAsync(s->v0_stage, p->v0, 2 * s->FN * sizeof(double), cudaMemcpyDefault, st));
     v0 = s->v0_stage;
   }
   FCA_CHECK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
-  FCA_CHECK_CUDA(counted(launch_prepare(s->M, s->storage, s->F, s->N, s->y, s->ginv, v0, s->v, s->vfloor,
-                                s->status, st)));
-  s->form = kFormS;
+  FCA_CHECK_CUDA(counted(launch_prepare(s->M, s->storage, s->F, s->N, y_direct ? p->y : s->y, s->ginv, v0,
+                                        s->v, s->vfloor, s->status, st, nullptr, &ex)));
+  s->form = kFormSP;
   s->prev_form = -1;
   s->failed = 0;
   s->last_iters = 0;
@@ -286,8 +311,8 @@ fca_status fca_em_fast(fca_state* s, int32_t iters, double* loglik_dev, void* st
     pa.lam = s->lam;
     pa.logdetS2 = s->logdetS2;
     FCA_CHECK_CUDA(counted(launch_gevd_from_S(s->M, pa, st)));
-    s->form = kFormP;
   }
+  s->form = kFormP;
   FastEmArgs a;
   std::memset(&a, 0, sizeof(a));
   a.F = s->F;
@@ -333,10 +358,8 @@ fca_status fca_em_fast_recover(fca_state* s, int32_t iters, double* loglik_dev, 
   pa.lam = s->lam;
   pa.logdetS2 = s->logdetS2;
   pa.S_out = s->S;
-  if (s->form == kFormS) {
-    FCA_CHECK_CUDA(counted(launch_gevd_from_S(s->M, pa, st)));
-    s->form = kFormP;
-  }
+  if (s->form == kFormS) FCA_CHECK_CUDA(counted(launch_gevd_from_S(s->M, pa, st)));
+  s->form = kFormP;
   FastEmArgs a;
   std::memset(&a, 0, sizeof(a));
   a.F = s->F;
@@ -388,8 +411,8 @@ fca_status fca_em_conventional(fca_state* s, int32_t iters, double* loglik_dev, 
     pa.lam = s->lam;
     pa.S_out = s->S;
     FCA_CHECK_CUDA(counted(launch_S_from_P(s->M, pa, st)));
-    s->form = kFormS;
   }
+  s->form = kFormS;
   ConvEmArgs a;
   std::memset(&a, 0, sizeof(a));
   a.F = s->F;

@@ -17,6 +17,18 @@ namespace fca {
 
 constexpr int kWarpsPerCta = 4;
 
+// 1/d for d > 0 by Newton-Raphson, r <- r + r (1 - d r), from the FP32 reciprocal of d: the
+// relative error squares each step, so two steps take the FP32 start (~2^-23) below FP64
+// rounding, at four FP64 FMAs instead of an FP64 division (several times their latency on
+// this GPU). Outside the FP32 normal range it divides.
+__device__ __forceinline__ double recip64(double d) {
+  if (!(d > 1e-36 && d < 1e36)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
 // In-place inverse of the M x M matrix in aug[.][0..M) (aug[.][M..2M) must hold I); the
 // inverse ends in aug[.][M..2M). Returns false (uniformly) if a pivot is zero.
 template <int M>
@@ -48,7 +60,8 @@ __device__ bool warp_inverse64(double2 (*aug)[2 * kMaxM], int lane) {
     __syncwarp();
     const double2 p = aug[k][k];
     const double dd = p.x * p.x + p.y * p.y;
-    const double2 inv = make_double2(p.x / dd, -p.y / dd);
+    const double rd = recip64(dd);
+    const double2 inv = make_double2(p.x * rd, -p.y * rd);
     __syncwarp();
     for (int j = lane; j < W; j += 32) aug[k][j] = zmul(aug[k][j], inv);
     __syncwarp();
@@ -73,6 +86,34 @@ __device__ bool warp_inverse64(double2 (*aug)[2 * kMaxM], int lane) {
   return true;
 }
 
+// One warp: (P, Lambda, log det S2) of bin f from (S1, S2) (Eq. (GEVD)); the bin's S is
+// also copied to S_copy when that is set. A failure leaves the bin's outputs unwritten and
+// records its status.
+template <int M>
+__device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double2* P, double* lam,
+                         double* logdetS2, int* status, WarpLA& la, float* sig, int lane) {
+  const size_t MM = (size_t)M * M;
+  for (int e = lane; e < M * M; e += 32) {
+    const double2 s1 = S[(size_t)f * MM + e], s2 = S[((size_t)F + f) * MM + e];
+    if (S_copy) {
+      S_copy[(size_t)f * MM + e] = s1;
+      S_copy[((size_t)F + f) * MM + e] = s2;
+    }
+    la.A[e / M][e % M] = z2c(s1);
+    la.L[e / M][e % M] = z2c(s2);
+  }
+  __syncwarp();
+  double ld = 0.0;
+  const int rc = warp_gevd<M>(la, lane, sig, &ld);
+  if (rc != kOk) {
+    if (lane == 0) set_status(status, rc);
+    return;
+  }
+  for (int e = lane; e < M * M; e += 32) P[(size_t)f * MM + e] = c2z(la.V[e / M][e % M]);
+  if (lane < M) lam[(size_t)f * M + lane] = (double)sig[lane];
+  if (lane == 0) logdetS2[f] = -ld;  // P = Q: log det S2 = -log|det P|^2
+}
+
 template <int M>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) gevd_from_S_kernel(const ParamArgs a) {
   __shared__ WarpLA la[kWarpsPerCta];
@@ -80,27 +121,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) gevd_from_S_kernel(const Pa
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int f = blockIdx.x * kWarpsPerCta + w;
   if (f >= a.F) return;  // whole warp leaves together
-  const size_t MM = (size_t)M * M;
-  for (int e = lane; e < M * M; e += 32) {
-    la[w].A[e / M][e % M] = z2c(a.S[(size_t)f * MM + e]);
-    la[w].L[e / M][e % M] = z2c(a.S[((size_t)a.F + f) * MM + e]);
-  }
-  __syncwarp();
-  double ld = 0.0;
-  const int rc = warp_gevd<M>(la[w], lane, sig[w], &ld);
-  if (rc != kOk) {
-    if (lane == 0) set_status(a.status, rc);
-    return;
-  }
-  for (int e = lane; e < M * M; e += 32) a.P[(size_t)f * MM + e] = c2z(la[w].V[e / M][e % M]);
-  if (lane < M) a.lam[(size_t)f * M + lane] = (double)sig[w][lane];
-  if (lane == 0) a.logdetS2[f] = -ld;  // P = Q: log det S2 = -log|det P|^2
+  gevd_bin<M>(a.S, nullptr, a.F, f, a.P, a.lam, a.logdetS2, a.status, la[w], sig[w], lane);
 }
 
 // mode 0: S_out = (P^-H Lam P^-1, P^-H P^-1); mode 1: separation prep.
 template <int M, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) from_P_kernel(const ParamArgs a) {
   __shared__ double2 aug[kWarpsPerCta][kMaxM][2 * kMaxM];
+  // The separation kernel that follows may start now: it waits for this grid's results.
+  if (MODE == 1) asm volatile("griddepcontrol.launch_dependents;");
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int f = blockIdx.x * kWarpsPerCta + w;
   if (f >= a.F) return;
@@ -142,13 +171,65 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) from_P_kernel(const ParamAr
   }
 }
 
-template <int M, int ST>
+// Sum of |y|^2 over the bin's N M values, taken by the 224 threads of warps 1..7 in one
+// fixed order whatever the path: value pairs (2i, 2i+1) go to thread i mod 224, which keeps
+// four partial sums and adds them at the end. 16-byte loads (and copies) when both addresses
+// allow them, else element by element in the same order. Also copies the values to yc.
+template <int ST>
+__device__ float bin_power(const typename Elem<ST>::T* yf, typename Elem<ST>::T* yc, int total, int t) {
+  using E = typename Elem<ST>::T;
+  constexpr int nt = 224;
+  const int n4 = total / 2;
+  const bool vec = ST == 0 && ((reinterpret_cast<uintptr_t>(yf) | reinterpret_cast<uintptr_t>(yc)) & 15) == 0;
+  auto pair = [&](int i) -> float4 {
+    if (vec) {
+      const float4 a = reinterpret_cast<const float4*>(yf)[i];
+      if (yc) reinterpret_cast<float4*>(yc)[i] = a;
+      return a;
+    }
+    const E e0 = yf[2 * i], e1 = yf[2 * i + 1];
+    if (yc) {
+      yc[2 * i] = e0;
+      yc[2 * i + 1] = e1;
+    }
+    const float2 u = decode(e0), w = decode(e1);
+    return make_float4(u.x, u.y, w.x, w.y);
+  };
+  auto acc = [](float4 a, float s) {
+    return fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, s))));
+  };
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int i = t;
+  for (; i + 3 * nt < n4; i += 4 * nt) {  // four loads in flight
+    const float4 a = pair(i), b = pair(i + nt), c = pair(i + 2 * nt), d = pair(i + 3 * nt);
+    s0 = acc(a, s0);
+    s1 = acc(b, s1);
+    s2 = acc(c, s2);
+    s3 = acc(d, s3);
+  }
+  for (; i < n4; i += nt) s0 = acc(pair(i), s0);
+  float s = s0 + ((s1 + s2) + s3);
+  if ((total & 1) && t == 0) {
+    const E e = yf[total - 1];
+    if (yc) yc[total - 1] = e;
+    s += cabs2(decode(e));
+  }
+  return s;
+}
+
+// One CTA (256 threads) per frequency bin: the positivity floor of v from the bin's mixture
+// power, the initial v clamped to it, and checks that both are finite. Warp 0 meanwhile
+// solves the bin's generalised eigenproblem when extra.S is set (PrepareExtra).
+template <int M, int ST, bool kX>
 __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void* y, const float* ginv,
                                                       const double* v0, float* v, float* vfloor,
-                                                      int* status, const BinDesc* bins) {
+                                                      int* status, const BinDesc* bins,
+                                                      const PrepareExtra ex) {
   using E = typename Elem<ST>::T;
   __shared__ double part[8];
   __shared__ float vf_s;
+  __shared__ WarpLA la;  // used (and kept) only by the kX variants
+  __shared__ float sig[kMaxM];
   const int tid = threadIdx.x;
   int f, N;
   size_t yoff, voff[2];
@@ -166,15 +247,19 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
     voff[0] = (size_t)f * N;
     voff[1] = (size_t)F * N + voff[0];
   }
-  const E* yf = reinterpret_cast<const E*>(y) + yoff;
   float s = 0.f;
-  for (int i = tid; i < N * M; i += 256) s += cabs2(decode(yf[i]));
+  if (tid >= 32) {
+    E* yc = (kX && ex.y_copy) ? reinterpret_cast<E*>(ex.y_copy) + yoff : nullptr;
+    s = bin_power<ST>(reinterpret_cast<const E*>(y) + yoff, yc, N * M, tid - 32);
+  } else if (kX && ex.S) {
+    gevd_bin<M>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, la, sig, tid);
+  }
   s = warp_sum(s);
   if ((tid & 31) == 0) part[tid >> 5] = (double)s;
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += part[w];
+    for (int w = 1; w < 8; ++w) t += part[w];
     const double g = (ST == 1) ? (double)ginv[f] : 1.0;
     t *= g * g;
     if (!isfinite(t)) set_status(status, kErrNonFinite);  // a NaN or infinity in the mixture
@@ -185,13 +270,15 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
   __syncthreads();
   const float vf = vf_s;
   int bad = 0;
-  for (int j = 0; j < 2; ++j)
+  for (int j = 0; j < 2; ++j) {
+#pragma unroll 4
     for (int n = tid; n < N; n += 256) {
       const size_t i = voff[j] + n;
       const double x = v0[i];
       bad |= !isfinite(x);
       v[i] = fmaxf((float)x, vf);
     }
+  }
   if (__syncthreads_or(bad) && tid == 0) set_status(status, kErrNonFinite);
 }
 
@@ -266,12 +353,21 @@ cudaError_t launch_sep_prep(int M, const ParamArgs& a, cudaStream_t st) {
 
 cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
                            const double* v0, float* v, float* vfloor, int* status, cudaStream_t st,
-                           const BinDesc* bins) {
+                           const BinDesc* bins, const PrepareExtra* extra) {
   if (F <= 0) return cudaSuccess;
+  if (extra && bins) return cudaErrorInvalidValue;  // the fused work assumes the [F][N][M] layout
+  const PrepareExtra ex = extra ? *extra : PrepareExtra{};
+  if (extra) {
+    if (storage) {
+      FCA_DISPATCH_M(M, (prepare_kernel<kM, 1, true><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
+    } else {
+      FCA_DISPATCH_M(M, (prepare_kernel<kM, 0, true><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
+    }
+  }
   if (storage) {
-    FCA_DISPATCH_M(M, (prepare_kernel<kM, 1><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins)); return cudaGetLastError())
+    FCA_DISPATCH_M(M, (prepare_kernel<kM, 1, false><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
   } else {
-    FCA_DISPATCH_M(M, (prepare_kernel<kM, 0><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins)); return cudaGetLastError())
+    FCA_DISPATCH_M(M, (prepare_kernel<kM, 0, false><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
   }
 }
 

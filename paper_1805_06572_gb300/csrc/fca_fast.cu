@@ -28,8 +28,19 @@ template <int M, int ST>
 static cudaError_t launch_sep_fast_m(const SepFastArgs& a, cudaStream_t st) {
   dim3 grid(a.F, (a.N + 255) / 256);  // bins on x (no 65535 limit), frame chunks on y
   if (a.N <= 0 || a.F <= 0) return cudaSuccess;
-  sep_fast_kernel<M, ST><<<grid, 256, 0, st>>>(a);
-  return cudaGetLastError();
+  // Launched as a programmatic dependent of the separation-constant kernel before it, so its
+  // CTAs start (and fetch y and v) while that kernel finishes.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sep_fast_kernel<M, ST>, a);
 }
 
 template <int ST>

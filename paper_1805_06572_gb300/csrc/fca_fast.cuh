@@ -495,6 +495,17 @@ __global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
   }
   const int n = blockIdx.y * 256 + tid;
   if (blockIdx.y * 256 >= N) return;  // whole CTA past this bin's frames
+  // The point's mixture and variances do not come from the kernel launched just before this
+  // one (the separation constants): read them first, then wait for that kernel's results
+  // (programmatic dependent launch; a plain launch order makes the wait return at once).
+  float2 yv[M];
+  float v1 = 0.f, v2 = 0.f;
+  if (n < N) {
+    load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + yoff + (size_t)n * M, yv);
+    v1 = a.v[v1off + n];
+    v2 = a.v[v2off + n];
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const size_t MM = (size_t)M * M;
   if (tid < M * M) {
     PH[tid / M][tid % M] = a.PH[f * MM + tid];
@@ -505,9 +516,6 @@ __global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
   if (n >= N) return;
   const size_t b = xoff + (size_t)n * M;
   const float gi = (ST == 1) ? a.ginv[f] : 1.f;
-  float2 yv[M];
-  load_bin<M, ST>(reinterpret_cast<const E*>(a.y) + yoff + (size_t)n * M, yv);
-  const float v1 = a.v[v1off + n], v2 = a.v[v2off + n];
   float2 mt[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
@@ -517,13 +525,30 @@ __global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
     const float e = v1 * lam[i];
     mt[i] = cscale(s, e / (e + v2));
   }
+  float2 o1[M], o2[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     float2 s = cmul(PiH[i][0], mt[0]);
 #pragma unroll
     for (int m = 1; m < M; ++m) s = cfma(PiH[i][m], mt[m], s);
-    a.x1[b + i] = s;
-    a.x2[b + i] = csub(cscale(yv[i], gi), s);
+    o1[i] = s;
+    o2[i] = csub(cscale(yv[i], gi), s);
+  }
+  float4* q1 = reinterpret_cast<float4*>(a.x1 + b);
+  float4* q2 = reinterpret_cast<float4*>(a.x2 + b);
+  if ((M & 1) == 0 && ((reinterpret_cast<uintptr_t>(q1) | reinterpret_cast<uintptr_t>(q2)) & 15) == 0) {
+    // 16-byte stores of complex pairs
+#pragma unroll
+    for (int i = 0; i < M / 2; ++i) {
+      q1[i] = make_float4(o1[2 * i].x, o1[2 * i].y, o1[2 * i + 1].x, o1[2 * i + 1].y);
+      q2[i] = make_float4(o2[2 * i].x, o2[2 * i].y, o2[2 * i + 1].x, o2[2 * i + 1].y);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      a.x1[b + i] = o1[i];
+      a.x2[b + i] = o2[i];
+    }
   }
 }
 

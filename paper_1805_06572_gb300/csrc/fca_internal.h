@@ -123,9 +123,23 @@ cudaError_t launch_sep_prep(int M, const ParamArgs& a, cudaStream_t st);
 
 // Positivity floor of v and conversion of the initial v (bins: nullptr for one mixture,
 // else F = number of bins and the descriptors give each bin's N and offsets).
+// Optional work fused into the prepare pass (single-mixture layout only, bins == nullptr):
+//   y_copy  receives a copy of y in the same layout (nullptr: none);
+//   S       when set, one warp of each bin's CTA solves the generalised eigenproblem of
+//           (S1, S2) into (P, lam, logdetS2) exactly as launch_gevd_from_S does, while the
+//           other warps stream y, and copies the bin's (S1, S2) to S_copy when that is set.
+struct PrepareExtra {
+  void* y_copy;
+  const double2* S;
+  double2* S_copy;
+  double2* P;
+  double* lam;
+  double* logdetS2;
+};
 cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
                            const double* v0, float* v, float* vfloor, int* status,
-                           cudaStream_t st, const BinDesc* bins = nullptr);
+                           cudaStream_t st, const BinDesc* bins = nullptr,
+                           const PrepareExtra* extra = nullptr);
 // out[mix_id[k] * iters + l] = sum of llf[l][b] over b in [b0[k], b0[k] + nb[k]), fixed order.
 cudaError_t launch_ll_ranges(int nmix, int iters, int F, const double* llf, const int* b0,
                              const int* nb, const int* mix_id, double* out, cudaStream_t st);

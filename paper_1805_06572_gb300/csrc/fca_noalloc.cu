@@ -126,16 +126,14 @@ extern "C" fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const
   // The array keeps the previous call's contents: the status word must start at zero; every
   // other region is written before it is read.
   NA_CHECK(cudaMemsetAsync(status, 0, sizeof(int), st));
-  NA_CHECK(fca::launch_prepare(M, FCA_STORE_C64, F, N, y_dev, nullptr, v0_dev, v_dev, vfloor, status, st));
-  fca::note_launches(1);
-  fca::ParamArgs pa = {};
-  pa.F = F;
-  pa.status = status;
-  pa.S = reinterpret_cast<const double2*>(S0_dev);
-  pa.P = P;
-  pa.lam = lam;
-  pa.logdetS2 = ldet;
-  NA_CHECK(fca::launch_gevd_from_S(M, pa, st));
+  // One pass: the floor and initial v, and the generalised eigenproblem of S0 (Eq. (GEVD)).
+  fca::PrepareExtra ex = {};
+  ex.S = reinterpret_cast<const double2*>(S0_dev);
+  ex.P = P;
+  ex.lam = lam;
+  ex.logdetS2 = ldet;
+  NA_CHECK(fca::launch_prepare(M, FCA_STORE_C64, F, N, y_dev, nullptr, v0_dev, v_dev, vfloor, status, st,
+                               nullptr, &ex));
   fca::note_launches(1);
   if (iters > 0) {
     fca::FastEmArgs a = {};

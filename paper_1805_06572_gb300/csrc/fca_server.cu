@@ -213,22 +213,22 @@ cudaError_t launch_request(fca_server* s, const fca_request& r, unsigned char* b
   S_TRY(cudaMemcpyAsync(S0, r.S0, 2 * (size_t)F * mm * 16, cudaMemcpyDefault, st));
   S_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
   int nk = 0;
-  S_TRY(launch_prepare(M, 0, F, N, y, nullptr, v0, v, vfloor, status, st));
+  // FastFCA requests solve the generalised eigenproblem of S0 (Eq. (GEVD)) in the same pass.
+  PrepareExtra ex;
+  std::memset(&ex, 0, sizeof(ex));
+  if (r.form == FCA_FORM_FAST) {
+    ex.S = S0;
+    ex.P = reinterpret_cast<double2*>(blk + L.P);
+    ex.lam = reinterpret_cast<double*>(blk + L.lam);
+    ex.logdetS2 = reinterpret_cast<double*>(blk + L.ldet);
+  }
+  S_TRY(launch_prepare(M, 0, F, N, y, nullptr, v0, v, vfloor, status, st, nullptr,
+                       r.form == FCA_FORM_FAST ? &ex : nullptr));
   ++nk;
   const bool res = em_resident(M, 0, N);
   const int res_bytes = res ? (int)em_dyn_smem(M, 0, N) : 0;
   double* llf = reinterpret_cast<double*>(blk + L.llf);
   if (r.form == FCA_FORM_FAST) {
-    ParamArgs pa;
-    std::memset(&pa, 0, sizeof(pa));
-    pa.F = F;
-    pa.status = status;
-    pa.S = S0;
-    pa.P = reinterpret_cast<double2*>(blk + L.P);
-    pa.lam = reinterpret_cast<double*>(blk + L.lam);
-    pa.logdetS2 = reinterpret_cast<double*>(blk + L.ldet);
-    S_TRY(launch_gevd_from_S(M, pa, st));
-    ++nk;
     if (it > 0) {
       FastEmArgs a;
       std::memset(&a, 0, sizeof(a));
@@ -241,9 +241,9 @@ cudaError_t launch_request(fca_server* s, const fca_request& r, unsigned char* b
       a.v_in = v;
       a.v = v;
       a.v_prev = v_prev;
-      a.P = pa.P;
-      a.lam = pa.lam;
-      a.logdetS2 = pa.logdetS2;
+      a.P = ex.P;
+      a.lam = ex.lam;
+      a.logdetS2 = ex.logdetS2;
       a.P_prev = reinterpret_cast<double2*>(blk + L.P_prev);
       a.lam_prev = reinterpret_cast<double*>(blk + L.lam_prev);
       a.logdetS2_prev = reinterpret_cast<double*>(blk + L.ldet_prev);
@@ -256,8 +256,8 @@ cudaError_t launch_request(fca_server* s, const fca_request& r, unsigned char* b
     std::memset(&sp, 0, sizeof(sp));
     sp.F = F;
     sp.status = status;
-    sp.P = it > 0 ? reinterpret_cast<double2*>(blk + L.P_prev) : pa.P;
-    sp.lam = it > 0 ? reinterpret_cast<double*>(blk + L.lam_prev) : pa.lam;
+    sp.P = it > 0 ? reinterpret_cast<double2*>(blk + L.P_prev) : ex.P;
+    sp.lam = it > 0 ? reinterpret_cast<double*>(blk + L.lam_prev) : ex.lam;
     sp.PH = reinterpret_cast<float2*>(blk + L.PH);
     sp.PinvH = reinterpret_cast<float2*>(blk + L.PinvH);
     sp.lam32 = reinterpret_cast<float*>(blk + L.lam32);
