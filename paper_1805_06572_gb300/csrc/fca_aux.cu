@@ -10,6 +10,8 @@
 //   ll_reduce   : per-iteration log-likelihood summed over frequencies in a fixed order.
 // One warp handles one frequency bin; P^-1 is formed by Gauss-Jordan elimination with
 // partial pivoting in FP64 (these kernels run once per call, not once per iteration).
+#include <type_traits>
+
 #include "fca_dev.cuh"
 #include "fca_internal.h"
 
@@ -86,12 +88,14 @@ __device__ bool warp_inverse64(double2 (*aug)[2 * kMaxM], int lane) {
   return true;
 }
 
-// One warp: (P, Lambda, log det S2) of bin f from (S1, S2) (Eq. (GEVD)); the bin's S is
-// also copied to S_copy when that is set. A failure leaves the bin's outputs unwritten and
-// records its status.
+// One warp: (P, Lambda, log det S2) of bin f from (S1, S2) (Eq. (GEVD)), by the solver the
+// EM kernel runs every iteration (register-resident for M <= 4, shared-memory otherwise);
+// P = Q, log det S2 = -log|det Q|^2. The bin's S is also copied to S_copy when that is set.
+// A failure leaves the bin's outputs unwritten and records its status.
 template <int M>
 __device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double2* P, double* lam,
-                         double* logdetS2, int* status, WarpLA& la, float* sig, int lane) {
+                         double* logdetS2, int* status, WarpLA& la, float* sig,
+                         float2 (*Q)[kMaxM], float2 (*U)[kMaxM], int lane) {
   const size_t MM = (size_t)M * M;
   for (int e = lane; e < M * M; e += 32) {
     const double2 s1 = S[(size_t)f * MM + e], s2 = S[((size_t)F + f) * MM + e];
@@ -103,25 +107,33 @@ __device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double
     la.L[e / M][e % M] = z2c(s2);
   }
   __syncwarp();
-  double ld = 0.0;
-  const int rc = warp_gevd<M>(la, lane, sig, &ld);
+  float ldL = 0.f;
+  int rc;
+  if constexpr (M <= 4) {
+    rc = warp_gevd_reg<M>(la.A, la.L, sig, Q, U, &ldL, 2.0e-7f, 30, lane);
+  } else {
+    rc = warp_gevd_fast<M>(la, lane, sig, Q, U, &ldL);
+  }
+  __syncwarp();
   if (rc != kOk) {
     if (lane == 0) set_status(status, rc);
     return;
   }
-  for (int e = lane; e < M * M; e += 32) P[(size_t)f * MM + e] = c2z(la.V[e / M][e % M]);
+  const double ldQ = (double)ldL + unitarity_defect<M>(U, lane);
+  for (int e = lane; e < M * M; e += 32) P[(size_t)f * MM + e] = c2z(Q[e / M][e % M]);
   if (lane < M) lam[(size_t)f * M + lane] = (double)sig[lane];
-  if (lane == 0) logdetS2[f] = -ld;  // P = Q: log det S2 = -log|det P|^2
+  if (lane == 0) logdetS2[f] = -ldQ;  // P = Q: log det S2 = -log|det P|^2
 }
 
 template <int M>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) gevd_from_S_kernel(const ParamArgs a) {
   __shared__ WarpLA la[kWarpsPerCta];
   __shared__ float sig[kWarpsPerCta][kMaxM];
+  __shared__ float2 Q[kWarpsPerCta][kMaxM][kMaxM], U[kWarpsPerCta][kMaxM][kMaxM];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int f = blockIdx.x * kWarpsPerCta + w;
   if (f >= a.F) return;  // whole warp leaves together
-  gevd_bin<M>(a.S, nullptr, a.F, f, a.P, a.lam, a.logdetS2, a.status, la[w], sig[w], lane);
+  gevd_bin<M>(a.S, nullptr, a.F, f, a.P, a.lam, a.logdetS2, a.status, la[w], sig[w], Q[w], U[w], lane);
 }
 
 // mode 0: S_out = (P^-H Lam P^-1, P^-H P^-1); mode 1: separation prep.
@@ -173,41 +185,73 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) from_P_kernel(const ParamAr
 
 // Sum of |y|^2 over the bin's N M values, taken by the 224 threads of warps 1..7 in one
 // fixed order whatever the path: value pairs (2i, 2i+1) go to thread i mod 224, which keeps
-// four partial sums and adds them at the end. 16-byte loads (and copies) when both addresses
-// allow them, else element by element in the same order. Also copies the values to yc.
-template <int ST>
-__device__ float bin_power(const typename Elem<ST>::T* yf, typename Elem<ST>::T* yc, int total, int t) {
+// four partial sums and adds them at the end. VEC: 16-byte loads (and copies), when both
+// addresses allow them; else element by element, same order. Also copies the values to yc;
+// the loads of a group come before its stores (the compiler may not assume yf and yc
+// disjoint).
+template <int ST, bool VEC>
+__device__ float bin_power_impl(const typename Elem<ST>::T* yf, typename Elem<ST>::T* yc, int total, int t) {
   using E = typename Elem<ST>::T;
+  using P = typename std::conditional<VEC, float4, E[2]>::type;
   constexpr int nt = 224;
   const int n4 = total / 2;
-  const bool vec = ST == 0 && ((reinterpret_cast<uintptr_t>(yf) | reinterpret_cast<uintptr_t>(yc)) & 15) == 0;
-  auto pair = [&](int i) -> float4 {
-    if (vec) {
-      const float4 a = reinterpret_cast<const float4*>(yf)[i];
-      if (yc) reinterpret_cast<float4*>(yc)[i] = a;
-      return a;
+  auto load = [&](int i, P& p) {
+    if constexpr (VEC) {
+      p = reinterpret_cast<const float4*>(yf)[i];
+    } else {
+      p[0] = yf[2 * i];
+      p[1] = yf[2 * i + 1];
     }
-    const E e0 = yf[2 * i], e1 = yf[2 * i + 1];
-    if (yc) {
-      yc[2 * i] = e0;
-      yc[2 * i + 1] = e1;
-    }
-    const float2 u = decode(e0), w = decode(e1);
-    return make_float4(u.x, u.y, w.x, w.y);
   };
-  auto acc = [](float4 a, float s) {
+  auto store = [&](int i, const P& p) {
+    if (!yc) return;
+    if constexpr (VEC) {
+      reinterpret_cast<float4*>(yc)[i] = p;
+    } else {
+      yc[2 * i] = p[0];
+      yc[2 * i + 1] = p[1];
+    }
+  };
+  auto acc = [](const P& p, float s) {
+    float4 a;
+    if constexpr (VEC) {
+      a = p;
+    } else {
+      const float2 u = decode(p[0]), w = decode(p[1]);
+      a = make_float4(u.x, u.y, w.x, w.y);
+    }
     return fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, s))));
   };
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   int i = t;
-  for (; i + 3 * nt < n4; i += 4 * nt) {  // four loads in flight
-    const float4 a = pair(i), b = pair(i + nt), c = pair(i + 2 * nt), d = pair(i + 3 * nt);
-    s0 = acc(a, s0);
-    s1 = acc(b, s1);
-    s2 = acc(c, s2);
-    s3 = acc(d, s3);
+  for (; i + 7 * nt < n4; i += 8 * nt) {  // eight loads in flight
+    P q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) load(i + k * nt, q[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) store(i + k * nt, q[k]);
+    s0 = acc(q[4], acc(q[0], s0));
+    s1 = acc(q[5], acc(q[1], s1));
+    s2 = acc(q[6], acc(q[2], s2));
+    s3 = acc(q[7], acc(q[3], s3));
   }
-  for (; i < n4; i += nt) s0 = acc(pair(i), s0);
+  for (; i + 3 * nt < n4; i += 4 * nt) {
+    P q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) load(i + k * nt, q[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) store(i + k * nt, q[k]);
+    s0 = acc(q[0], s0);
+    s1 = acc(q[1], s1);
+    s2 = acc(q[2], s2);
+    s3 = acc(q[3], s3);
+  }
+  for (; i < n4; i += nt) {
+    P p;
+    load(i, p);
+    store(i, p);
+    s0 = acc(p, s0);
+  }
   float s = s0 + ((s1 + s2) + s3);
   if ((total & 1) && t == 0) {
     const E e = yf[total - 1];
@@ -217,19 +261,28 @@ __device__ float bin_power(const typename Elem<ST>::T* yf, typename Elem<ST>::T*
   return s;
 }
 
+template <int ST>
+__device__ float bin_power(const typename Elem<ST>::T* yf, typename Elem<ST>::T* yc, int total, int t) {
+  const bool vec = ST == 0 && ((reinterpret_cast<uintptr_t>(yf) | reinterpret_cast<uintptr_t>(yc)) & 15) == 0;
+  return vec ? bin_power_impl<ST, true>(yf, yc, total, t) : bin_power_impl<ST, false>(yf, yc, total, t);
+}
+
 // One CTA (256 threads) per frequency bin: the positivity floor of v from the bin's mixture
-// power, the initial v clamped to it, and checks that both are finite. Warp 0 meanwhile
-// solves the bin's generalised eigenproblem when extra.S is set (PrepareExtra).
+// power, the initial v clamped to it, and checks that both are finite, all on warps 1..7
+// (synchronised among themselves by named barrier 1). Warp 0 meanwhile solves the bin's
+// generalised eigenproblem when extra.S is set (PrepareExtra).
 template <int M, int ST, bool kX>
 __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void* y, const float* ginv,
                                                       const double* v0, float* v, float* vfloor,
                                                       int* status, const BinDesc* bins,
                                                       const PrepareExtra ex) {
   using E = typename Elem<ST>::T;
+  constexpr int kStreamThreads = 224;
   __shared__ double part[8];
   __shared__ float vf_s;
   __shared__ WarpLA la;  // used (and kept) only by the kX variants
   __shared__ float sig[kMaxM];
+  __shared__ float2 Qs[kMaxM][kMaxM], Us[kMaxM][kMaxM];
   const int tid = threadIdx.x;
   int f, N;
   size_t yoff, voff[2];
@@ -247,36 +300,49 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
     voff[0] = (size_t)f * N;
     voff[1] = (size_t)F * N + voff[0];
   }
-  float s = 0.f;
-  if (tid >= 32) {
-    E* yc = (kX && ex.y_copy) ? reinterpret_cast<E*>(ex.y_copy) + yoff : nullptr;
-    s = bin_power<ST>(reinterpret_cast<const E*>(y) + yoff, yc, N * M, tid - 32);
-  } else if (kX && ex.S) {
-    gevd_bin<M>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, la, sig, tid);
-  }
-  s = warp_sum(s);
-  if ((tid & 31) == 0) part[tid >> 5] = (double)s;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 1; w < 8; ++w) t += part[w];
-    const double g = (ST == 1) ? (double)ginv[f] : 1.0;
-    t *= g * g;
-    if (!isfinite(t)) set_status(status, kErrNonFinite);  // a NaN or infinity in the mixture
-    const double fl = fmax(1e-12 * t / ((double)N * M), 1e-30);
-    vf_s = (float)fl;
-    vfloor[f] = (float)fl;
-  }
-  __syncthreads();
-  const float vf = vf_s;
   int bad = 0;
-  for (int j = 0; j < 2; ++j) {
-#pragma unroll 4
-    for (int n = tid; n < N; n += 256) {
-      const size_t i = voff[j] + n;
-      const double x = v0[i];
-      bad |= !isfinite(x);
-      v[i] = fmaxf((float)x, vf);
+  if (tid < 32) {
+    if (kX && ex.S) gevd_bin<M>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, la, sig, Qs, Us, tid);
+  } else {
+    const int t = tid - 32;
+    E* yc = (kX && ex.y_copy) ? reinterpret_cast<E*>(ex.y_copy) + yoff : nullptr;
+    float s = bin_power<ST>(reinterpret_cast<const E*>(y) + yoff, yc, N * M, t);
+    s = warp_sum(s);
+    if ((tid & 31) == 0) part[tid >> 5] = (double)s;
+    asm volatile("bar.sync 1, 224;" ::: "memory");
+    if (t == 0) {
+      double tot = 0.0;
+      for (int w = 1; w < 8; ++w) tot += part[w];
+      const double g = (ST == 1) ? (double)ginv[f] : 1.0;
+      tot *= g * g;
+      if (!isfinite(tot)) set_status(status, kErrNonFinite);  // a NaN or infinity in the mixture
+      const double fl = fmax(1e-12 * tot / ((double)N * M), 1e-30);
+      vf_s = (float)fl;
+      vfloor[f] = (float)fl;
+    }
+    asm volatile("bar.sync 1, 224;" ::: "memory");
+    const float vf = vf_s;
+    // Both sources' values, four frames each, loaded before any store (v and v0 may not be
+    // assumed disjoint by the compiler).
+    for (int n0 = t; n0 < N; n0 += 4 * kStreamThreads) {
+      double x[2][4];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int n = n0 + k * kStreamThreads;
+          x[j][k] = n < N ? v0[voff[j] + n] : 1.0;
+        }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int n = n0 + k * kStreamThreads;
+          if (n < N) {
+            bad |= !isfinite(x[j][k]);
+            v[voff[j] + n] = fmaxf((float)x[j][k], vf);
+          }
+        }
     }
   }
   if (__syncthreads_or(bad) && tid == 0) set_status(status, kErrNonFinite);

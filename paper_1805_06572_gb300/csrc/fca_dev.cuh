@@ -295,207 +295,13 @@ __device__ bool warp_cholesky(WarpLA& la, int lane) {
   return true;
 }
 
-// la.A <- L^-1 A L^-H for Hermitian A (in la.A), using la.L / la.invd; la.Z and la.V are
-// clobbered.
-template <int M>
-__device__ void warp_congruence_inv(WarpLA& la, int lane) {
-  if (lane < M) {  // Z = L^-1 A, column `lane`
-    const int c = lane;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      float2 s = la.A[i][c];
-#pragma unroll
-      for (int m = 0; m < i; ++m) s = csub(s, cmul(la.L[i][m], la.Z[m][c]));
-      la.Z[i][c] = cscale(s, la.invd[i]);
-    }
-  }
-  __syncwarp();
-  if (lane < M) {  // V = L^-1 Z^H, column `lane` (Z^H = A L^-H since A is Hermitian)
-    const int c = lane;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      float2 s = cconj(la.Z[c][i]);
-#pragma unroll
-      for (int m = 0; m < i; ++m) s = csub(s, cmul(la.L[i][m], la.V[m][c]));
-      la.V[i][c] = cscale(s, la.invd[i]);
-    }
-  }
-  __syncwarp();
-  // Hermitian part into A.
-  for (int e = lane; e < M * M; e += 32) {
-    const int i = e / M, j = e - (e / M) * M;
-    float2 a = la.V[i][j], b = la.V[j][i];
-    la.A[i][j] = (i == j) ? make_float2(a.x, 0.f) : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-  }
-  __syncwarp();
-}
-
-// Cyclic Jacobi eigendecomposition of the Hermitian matrix in la.A: on return la.A is
-// (numerically) diagonal with the eigenvalues on its diagonal and la.V holds the
-// eigenvectors (A_in = V diag V^H). Rotations use the round-robin ordering, so the M/2
-// rotations of one round are disjoint and applied together by all lanes. A pair is rotated
-// when |a_pq|^2 > tol^2 |a_pp a_qq|. Returns the number of sweeps, or -1 on the sweep cap.
-template <int M>
-__device__ int warp_jacobi(WarpLA& la, int lane, float tol, int max_sweeps) {
-  constexpr int n = M + (M & 1);  // even number of positions (a dummy index when M is odd)
-  for (int e = lane; e < M * M; e += 32) {
-    const int i = e / M, j = e - (e / M) * M;
-    la.V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-  }
-  __syncwarp();
-  if (M == 1) return 0;
-  const float tol2 = tol * tol;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    int rotated = 0;
-    float worst = 0.f;  // largest |a_pq|^2 / |a_pp a_qq| met in this sweep
-    for (int r = 0; r < n - 1; ++r) {
-      if (lane < n / 2) {
-        const int k = lane;
-        const int a = (k == 0) ? r : (r + k) % (n - 1);
-        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
-        const int p = min(a, b), q = max(a, b);
-        float c = 1.f, s = 0.f;
-        float2 e = make_float2(1.f, 0.f);
-        if (q < M) {
-          const float app = la.A[p][p].x, aqq = la.A[q][q].x;
-          const float2 apq = la.A[p][q];
-          const float r2 = cabs2(apq);
-          const float den = fabsf(app * aqq);
-          if (r2 > tol2 * den && r2 > 1e-36f) {
-            worst = fmaxf(worst, den > 0.f ? __fdividef(r2, den) : 1.f);
-            // 1/|a_pq| and c = 1/sqrt(1+t^2) each get one Newton step after the approximate
-            // reciprocal square root, so that |e| = 1 and c^2 + s^2 = 1 hold to rounding:
-            // a biased error there would make U non-unitary in the same direction every
-            // rotation and shift the scale of the implied S2.
-            float ir = rsqrtf(r2);
-            ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);   // 1 / |a_pq|
-            const float tau = 0.5f * (aqq - app) * ir;
-            const float h = fmaf(tau, tau, 1.f);
-            const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
-            const float g = fmaf(t, t, 1.f);
-            c = rsqrtf(g);
-            c = c * fmaf(-0.5f * g * c, c, 1.5f);
-            s = t * c;
-            e = cscale(apq, ir);
-            rotated = 1;
-          }
-          // J_pp = c, J_qp = -s conj(e), J_pq = s, J_qq = c conj(e)
-          la.jself[p] = make_float2(c, 0.f);
-          la.joth[p] = cscale(cconj(e), -s);
-          la.partner[p] = q;
-          la.jself[q] = cscale(cconj(e), c);
-          la.joth[q] = make_float2(s, 0.f);
-          la.partner[q] = p;
-        } else {
-          la.jself[p] = make_float2(1.f, 0.f);
-          la.joth[p] = make_float2(0.f, 0.f);
-          la.partner[p] = p;
-        }
-      }
-      __syncwarp();
-      // new A_il = conj(J_ii)(A_il J_ll + A_il' J_l'l) + conj(J_i'i)(A_i'l J_ll + A_i'l' J_l'l)
-      constexpr int kPer = (M * M + 31) / 32;
-      float2 na[kPer], nv[kPer];
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        const int e = lane + 32 * t;
-        if (e < M * M) {
-          const int i = e / M, l = e - (e / M) * M;
-          const int ip = la.partner[i], lp = la.partner[l];
-          const float2 Ji = la.jself[i], Jo_i = la.joth[i], Jl = la.jself[l], Jo_l = la.joth[l];
-          const float2 r0 = cfma(la.A[i][lp], Jo_l, cmul(la.A[i][l], Jl));
-          const float2 r1 = cfma(la.A[ip][lp], Jo_l, cmul(la.A[ip][l], Jl));
-          na[t] = cadd(ccmul(Ji, r0), ccmul(Jo_i, r1));
-          nv[t] = cfma(la.V[i][lp], Jo_l, cmul(la.V[i][l], Jl));
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        const int e = lane + 32 * t;
-        if (e < M * M) {
-          const int i = e / M, l = e - (e / M) * M;
-          float2 v = na[t];
-          if (i == l) v.y = 0.f;
-          else if (la.partner[i] == l) v = make_float2(0.f, 0.f);  // the pivot pair
-          la.A[i][l] = v;
-          la.V[i][l] = nv[t];
-        }
-      }
-      __syncwarp();
-    }
-    // Stop when nothing rotated, or when every rotation of this sweep started from a relative
-    // off-diagonal below 1e-4: cyclic Jacobi converges quadratically, so the next sweep would
-    // meet off-diagonals of order 1e-8 and rotate nothing.
-    if (!__any_sync(0xffffffffu, rotated)) return sweep + 1;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-    if (worst <= 1e-8f) return sweep + 1;
-  }
-  return -1;
-}
-
-// la.V <- L^-H la.V (back substitution, one column per lane).
-template <int M>
-__device__ void warp_backsolve_LH(WarpLA& la, int lane) {
-  if (lane < M) {
-    const int c = lane;
-    float2 q[M];
-#pragma unroll
-    for (int i = M - 1; i >= 0; --i) {
-      float2 s = la.V[i][c];
-#pragma unroll
-      for (int m = i + 1; m < M; ++m) s = csub(s, ccmul(la.L[m][i], q[m]));
-      q[i] = cscale(s, la.invd[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < M; ++i) la.Z[i][c] = q[i];
-  }
-  __syncwarp();
-  for (int e = lane; e < M * M; e += 32) {
-    const int i = e / M, j = e - (e / M) * M;
-    la.V[i][j] = la.Z[i][j];
-  }
-  __syncwarp();
-}
-
+// ---------------------------------------------------------------- low-latency solver
 // Generalised eigenproblem of the Hermitian pencil (A, B), B positive definite, given in
 // la.A (A) and la.L (B): Cholesky B = L L^H, W = L^-1 A L^-H = U Sig U^H (Jacobi),
-// Q = L^-H U, so that Q^H B Q = I and Q^H A Q = Sig (Eq. (GEVDeff5)). On return la.V = Q and
-// sig[i] = Sig_ii. *logdetQ receives log|det Q|^2 of the Q actually returned:
+// Q = L^-H U, so that Q^H B Q = I and Q^H A Q = Sig (Eq. (GEVDeff5)). log|det Q|^2 =
 // 2 sum_i log(1/L_ii) + log|det U|^2, where the FP32 rotations leave U unitary only to
-// rounding, so
-// log|det U|^2 = log det(U^H U) = ||U||_F^2 - M to first order in U^H U - I (FP64 sum).
-// Returns a device status code.
-template <int M>
-__device__ int warp_gevd(WarpLA& la, int lane, float* sig, double* logdetQ) {
-  if (!warp_cholesky<M>(la, lane)) return kErrNotPD;
-  // log|det L^-H|^2 from the reciprocal pivots the solves below actually apply.
-  float ld = (lane < M) ? 2.f * logf(la.invd[lane]) : 0.f;
-  ld = warp_sum(ld);
-  warp_congruence_inv<M>(la, lane);
-  const int sw = warp_jacobi<M>(la, lane, 2.0e-7f, 30);
-  if (sw < 0) return kErrEigNoConv;
-  if (lane < M) sig[lane] = la.A[lane][lane].x;
-  double un = 0.0;
-  for (int e = lane; e < M * M; e += 32) {
-    const float2 u = la.V[e / M][e % M];
-    un = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, un));
-  }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) un += __shfl_xor_sync(0xffffffffu, un, o);
-  warp_backsolve_LH<M>(la, lane);
-  __syncwarp();
-  *logdetQ = (un - (double)M) + (double)ld;
-  for (int i = 0; i < M; ++i) {
-    const float s = sig[i];
-    if (!(s > 0.f) || !(s < 3.0e38f)) return kErrNotPD;
-  }
-  return kOk;
-}
-
-// ---------------------------------------------------------------- low-latency solver
-// The same generalised eigenproblem as warp_gevd, arranged for a short dependency chain:
+// rounding, so log|det U|^2 = log det(U^H U) = ||U||_F^2 - M to first order in U^H U - I.
+// Arranged for a short dependency chain:
 // one lane factors B = L L^H and inverts L in registers (no warp synchronisation inside the
 // recurrences), the congruence W = L^-1 A L^-H and Q = L^-H U are lane-parallel products,
 // and the Jacobi rounds ping-pong between two copies of A and V (one __syncwarp fewer per
