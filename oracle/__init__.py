@@ -5,8 +5,8 @@ import this package. It is a plain complex128 C++ implementation of both forms o
 (conventional, Sec. 2; FastFCA, Sec. 3 and Algorithm 1) plus the Appendix's constructive
 generalised eigendecomposition. It shares no code with the CUDA library.
 
-Parity status of each function is listed in the design doc; every function here is pinned by
-the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
+Every function here is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``
+(closed forms, library routines, invariants and brute force on tiny inputs).
 """
 from __future__ import annotations
 
