@@ -193,6 +193,12 @@ def hbm_model(M, value):
             "frac": gbs / peak}
 
 
+def mid_workload(c) -> str:
+    """The headline workload's description, shared by both arms."""
+    return (f"M={c.M} F={c.F} N={c.N} L={c.iters}, 2 sources, complex64, seeded mixture per rank "
+            f"(delta={c.delta}, sigma={c.sigma})")
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle timed on the host cores, one bounded sample per step."""
     import synth
@@ -216,8 +222,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"M={c.M} F={c.F} N={c.N} L={c.iters}, 2 sources, sampled bins",
-                   "form": "FastFCA (oracle)"},
+        "config": {"workload": mid_workload(c), "form": "FastFCA (FP64 oracle, host cores)",
+                   "step": "L iterations with log-likelihood + posterior means, every bin"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -730,8 +736,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": max_over_ranks(statistics.mean(ms_fast)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"M={M} F={F} N={N} L={L}, 2 sources, complex64, seeded mixture "
-                               f"per rank (delta={c.delta}, sigma={c.sigma})",
+        "config": {"workload": mid_workload(c),
                    "form": "FastFCA", "l2": "flushed between steps (256 MiB write, outside the "
                    "step events)", "parallelism": f"replicas x{world}",
                    "step": "load + initial GEVD + L iterations with log-likelihood + "
