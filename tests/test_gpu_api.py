@@ -192,3 +192,39 @@ def test_nan_in_the_mixture_is_reported_and_latched(fca, form):
     fca.fca_load(st, *to_dev(yc, v0c, S0c))
     em(st, 3)
     assert fca.fca_sync_status(st) == 0
+
+
+@pytest.mark.parametrize("form,M", [("fast", 4), ("fast", 3), ("conventional", 4)])
+def test_results_do_not_depend_on_input_alignment(fca, form, M):
+    """The load pass reads device inputs in place (16-byte loads where the addresses allow,
+    element by element otherwise, in one summation order either way), and falls back to a
+    copy for inputs not aligned to their element. Views offset by one element give bitwise
+    the results of aligned inputs."""
+    y, v0, S0 = problem(seed=33, M=M, F=6, N=301)  # M = 3: an odd count of values per bin
+    F, N, M = y.shape
+    d = torch.device("cuda")
+
+    def offset_view(a, dtype):
+        t = torch.empty(a.size + 1, dtype=dtype, device=d)
+        t[1:] = torch.from_numpy(a.ravel()).to(d)
+        return t[1:].view(a.shape)
+
+    def run(yd, vd, Sd):
+        st = fca.fca_init(yd, vd, Sd)
+        ll = torch.empty(5, dtype=torch.float64, device=d)
+        (fca.fca_em_fast if form == "fast" else fca.fca_em_conventional)(st, 5, ll)
+        x1 = torch.empty((F, N, M), dtype=torch.complex64, device=d)
+        x2 = torch.empty_like(x1)
+        fca.fca_separate(st, x1, x2, fca.FCA_SEP_ALG1)
+        v = torch.empty((2, F, N), dtype=torch.float32, device=d)
+        fca.fca_get_params(st, v=v)
+        assert fca.fca_sync_status(st) == 0
+        out = [t.cpu().numpy() for t in (x1, x2, v, ll)]
+        fca.fca_free(st)
+        return out
+
+    ref = run(*to_dev(y, v0, S0))
+    got = run(offset_view(y, torch.complex64), offset_view(v0, torch.float64),
+              offset_view(S0, torch.complex128))
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
