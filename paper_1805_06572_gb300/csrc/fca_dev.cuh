@@ -402,9 +402,14 @@ __device__ void warp_congruence_products(WarpLA& la, int lane) {
   __syncwarp();
 }
 
-// Jacobi as warp_jacobi, reading A/V from one buffer and writing the other each round.
-// On return the current buffers are la.A / la.V (an even number of swaps is enforced by
-// a final copy when needed).
+// Cyclic complex Jacobi on the Hermitian la.A, eigenvectors accumulated in la.V, in
+// round-robin order (each round rotates disjoint pivot pairs at once). For a pivot (p, q)
+// with a_pq = |a_pq| e: tau = (a_qq - a_pp) / (2 |a_pq|), t = sign(tau) / (|tau| +
+// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, and J_pp = c, J_pq = s,
+// J_qp = -s conj(e), J_qq = c conj(e) zeroes a_pq: A <- J^H A J, V <- V J. Pivots below
+// tol relative to sqrt(|a_pp a_qq|) are skipped. Each round reads A/V from one buffer and
+// writes the other; on return the current buffers are la.A / la.V (an even number of swaps is
+// enforced by a final copy when needed).
 template <int M>
 __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
   constexpr int n = M + (M & 1);
@@ -599,235 +604,6 @@ __device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[k
   return kOk;
 }
 
-// Single-lane version of warp_gevd_fast for small M: the whole generalised eigenproblem in
-// one thread's registers (Cholesky and its inverse, the congruence, a cyclic Jacobi on the
-// upper triangle, Q = L^-H U), with no warp synchronisation or shared-memory round trips.
-// At M <= 4 a parallel Jacobi round costs more in synchronisation than its rotations.
-// Inputs A, B (Hermitian, B positive definite) are read from shared memory; outputs as
-// warp_gevd_fast. Returns a device status code.
-template <int M>
-__device__ int lane_gevd(const float2 (*A)[kMaxM], const float2 (*B)[kMaxM], float* sig,
-                         float2 (*Qout)[kMaxM], float2 (*Uout)[kMaxM], float* ldL, float tol,
-                         int max_sweeps) {
-  // Cholesky B = L L^H and L^-1.
-  float2 L[M][M];
-  float id[M];
-  bool good = true;
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-#pragma unroll
-    for (int i = j; i < M; ++i) {
-      float2 sv = B[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) sv = csub(sv, cmulc(L[i][k], L[j][k]));
-      if (i == j) {
-        const float piv = sv.x;
-        good = good && (piv > 0.f) && (piv < 3.0e38f);
-        float il = rsqrtf(piv);
-        il = il * fmaf(-0.5f * piv * il, il, 1.5f);
-        id[j] = il;
-        L[j][j] = make_float2(piv * il, 0.f);
-      } else {
-        L[i][j] = cscale(sv, id[j]);
-      }
-    }
-  }
-  if (!good) return kErrNotPD;
-  float2 Li[M][M];
-  float ld = 0.f;
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    Li[j][j] = make_float2(id[j], 0.f);
-    ld += 2.f * logf(id[j]);
-#pragma unroll
-    for (int i = j + 1; i < M; ++i) {
-      float2 sv = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = j; k < i; ++k) sv = cfma(L[i][k], Li[k][j], sv);
-      Li[i][j] = cscale(sv, -id[i]);
-    }
-  }
-  // W = Li A Li^H: T = A Li^H, then the upper triangle of Li T.
-  float2 T[M][M];
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-      float2 sv = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k <= j; ++k) sv = cadd(sv, cmulc(A[i][k], Li[j][k]));
-      T[i][j] = sv;
-    }
-  float2 W[M][M];  // only i <= j is kept up to date
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-#pragma unroll
-    for (int j = i; j < M; ++j) {
-      float2 sv = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k <= i; ++k) sv = cfma(Li[i][k], T[k][j], sv);
-      W[i][j] = (i == j) ? make_float2(sv.x, 0.f) : sv;
-    }
-  float2 V[M][M];
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-#pragma unroll
-    for (int j = 0; j < M; ++j) V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-  // Cyclic Jacobi in round-robin order: each round rotates disjoint pivot pairs, whose
-  // angles depend only on their own 2 x 2 blocks, so the angle computations of a round are
-  // independent dependency chains (the rotations are then applied one after the other).
-  // Rotation as in warp_jacobi: J_pp = c, J_pq = s, J_qp = -s conj(e), J_qq = c conj(e); rows
-  // p, q of W change by J^H, columns of V by J. Once every off-diagonal entry is below 2e-4 of
-  // its eigenvalue gap, the sweeps stop with one first-order step instead (polish below).
-  const float tol2 = tol * tol;
-  constexpr int n = M + (M & 1);  // even number of positions (a dummy index when M is odd)
-  constexpr int NP = n / 2;
-  int sweeps = -1;
-  if (M == 1) sweeps = 0;
-  for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
-    bool rotated = false, big = false;
-#pragma unroll
-    for (int r = 0; r < n - 1; ++r) {
-      float cs[NP], sn[NP], tt[NP], rr[NP], app[NP], aqq[NP];
-      float2 ee[NP];
-      bool act[NP];
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        const int a = (k == 0) ? r : (r + k) % (n - 1);
-        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
-        const int p = a < b ? a : b, q = a < b ? b : a;
-        act[k] = false;
-        if (q >= M) continue;
-        app[k] = W[p][p].x;
-        aqq[k] = W[q][q].x;
-        const float2 apq = W[p][q];
-        const float r2 = cabs2(apq);
-        const float den = fabsf(app[k] * aqq[k]);
-        if (r2 > tol2 * den && r2 > 1e-36f) {
-          act[k] = true;
-          rotated = true;
-          big = big || (r2 > 1e-8f * den);
-          float ir = rsqrtf(r2);
-          ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
-          const float tau = 0.5f * (aqq[k] - app[k]) * ir;
-          const float h = fmaf(tau, tau, 1.f);
-          const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
-          const float g = fmaf(t, t, 1.f);
-          float c = rsqrtf(g);
-          c = c * fmaf(-0.5f * g * c, c, 1.5f);
-          cs[k] = c;
-          sn[k] = t * c;
-          tt[k] = t;
-          rr[k] = r2 * ir;  // |a_pq|
-          ee[k] = cscale(apq, ir);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        if (!act[k]) continue;
-        const int a = (k == 0) ? r : (r + k) % (n - 1);
-        const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
-        const int p = a < b ? a : b, q = a < b ? b : a;
-        const float c = cs[k], sv = sn[k];
-        const float2 e = ee[k];
-        const float2 mse = cscale(e, -sv);          // -s e
-        const float2 cec = cscale(cconj(e), c);     // c conj(e)
-        const float2 msec = cscale(cconj(e), -sv);  // -s conj(e)
-#pragma unroll
-        for (int m = 0; m < M; ++m) {  // off-block entries (p,m), (q,m): rows of J^H W
-          if (m == p || m == q) continue;
-          const float2 x = (p < m) ? W[p][m] : cconj(W[m][p]);
-          const float2 y = (q < m) ? W[q][m] : cconj(W[m][q]);
-          const float2 xn = cfma(mse, y, cscale(x, c));
-          const float2 yn = cfma(cconj(cec), y, cscale(x, sv));
-          if (p < m) W[p][m] = xn; else W[m][p] = cconj(xn);
-          if (q < m) W[q][m] = yn; else W[m][q] = cconj(yn);
-        }
-        W[p][p] = make_float2(app[k] - tt[k] * rr[k], 0.f);
-        W[q][q] = make_float2(aqq[k] + tt[k] * rr[k], 0.f);
-        W[p][q] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < M; ++m) {  // V <- V J
-          const float2 vp = V[m][p], vq = V[m][q];
-          V[m][p] = cfma(vq, msec, cscale(vp, c));
-          V[m][q] = cfma(vq, cec, cscale(vp, sv));
-        }
-      }
-    }
-    if (!rotated || !big) {  // this sweep started within 1e-4: what is left is below rounding
-      sweeps = sweep + 1;
-      break;
-    }
-    bool small = true;
-#pragma unroll
-    for (int p = 0; p < M - 1; ++p)
-#pragma unroll
-      for (int q = p + 1; q < M; ++q) {
-        const float gap = W[q][q].x - W[p][p].x;
-        small = small && (cabs2(W[p][q]) <= 4e-8f * gap * gap);
-      }
-    if (small) {
-      // First-order step: with W = D + E (E off-diagonal, |E_pq| <= 2e-4 |d_q - d_p|), the
-      // eigenvectors are I + X, X_pq = E_pq / (d_q - d_p) (X skew-Hermitian), up to O(|X|^2)
-      // = 4e-8 (below FP32 rounding), and the eigenvalues d_q + sum_p |E_pq|^2 / (d_q - d_p).
-      float2 X[M][M];
-      float d[M];
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        X[i][i] = make_float2(0.f, 0.f);
-        d[i] = W[i][i].x;
-      }
-#pragma unroll
-      for (int p = 0; p < M - 1; ++p)
-#pragma unroll
-        for (int q = p + 1; q < M; ++q) {
-          const float ig = __fdividef(1.f, d[q] - d[p]);
-          X[p][q] = cscale(W[p][q], ig);
-          X[q][p] = make_float2(-X[p][q].x, X[p][q].y);  // -conj(X_pq)
-          const float d2 = cabs2(W[p][q]) * ig;
-          W[q][q].x += d2;
-          W[p][p].x -= d2;
-        }
-      float2 Vn[M][M];
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-          float2 acc = V[i][j];
-#pragma unroll
-          for (int m = 0; m < M; ++m)
-            if (m != j) acc = cfma(V[i][m], X[m][j], acc);
-          Vn[i][j] = acc;
-        }
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-#pragma unroll
-        for (int j = 0; j < M; ++j) V[i][j] = Vn[i][j];
-      sweeps = sweep + 1;
-      break;
-    }
-  }
-  if (sweeps < 0) return kErrEigNoConv;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    sig[i] = W[i][i].x;
-    if (!(W[i][i].x > 0.f) || !(W[i][i].x < 3.0e38f)) good = false;
-  }
-  // Q = Li^H V: Q_ij = sum_{k>=i} conj(Li_ki) V_kj.
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-      float2 sv = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = i; k < M; ++k) sv = cadd(sv, ccmul(Li[k][i], V[k][j]));
-      Qout[i][j] = sv;
-      Uout[i][j] = V[i][j];
-    }
-  *ldL = ld;
-  return good ? kOk : kErrNotPD;
-}
-
 // ------------------------------------------------------ register-resident solver, M <= 4
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
@@ -842,14 +618,16 @@ __device__ __forceinline__ int rr_partner(int x, int r, int n) {
   return ((y % (n - 1)) + (n - 1)) % (n - 1);
 }
 
-// The generalised eigenproblem of lane_gevd (same contract, same outputs), with the work of
-// each step spread over the warp: lane l < M*M owns entry (l / M, l % M) of W = L^-1 A L^-H
-// and of the eigenvector matrix V, and reads the entries it needs from other lanes by
-// shuffles (no shared-memory round trips). Lane 0 factors B = L L^H and forms L^-1 (inherently
-// sequential recurrences) and writes L^-1 over B. Each Jacobi round rotates the disjoint
-// round-robin pairs at once (every lane computes the angle of its row's pair; the column's
-// comes by shuffle). Sweeps stop as in lane_gevd, or with the first-order step once every
-// off-diagonal entry is below 2e-4 of its eigenvalue gap. Called by all 32 lanes.
+// The generalised eigenproblem of warp_gevd_fast (same contract, same outputs: sig, Q = L^-H U,
+// U, 2 sum log(1/L_ii); a device status code) for M <= 4, with the work of each step spread
+// over the warp: lane l < M*M owns entry (l / M, l % M) of W = L^-1 A L^-H and of the
+// eigenvector matrix V, and reads the entries it needs from other lanes by shuffles (no
+// shared-memory round trips). Lane 0 factors B = L L^H and forms L^-1 (inherently sequential
+// recurrences) and writes L^-1 over B. Each Jacobi round (the rotation of warp_jacobi_pp)
+// rotates the disjoint round-robin pairs at once (every lane computes the angle of its row's
+// pair; the column's comes by shuffle). Sweeps stop when a sweep rotated nothing or no pivot
+// exceeded 1e-4 of sqrt(|a_pp a_qq|), or with the first-order step once every off-diagonal
+// entry is below 2e-4 of its eigenvalue gap. Called by all 32 lanes.
 template <int M>
 __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float* sig,
                              float2 (*Qout)[kMaxM], float2 (*Uout)[kMaxM], float* ldL, float tol,
@@ -997,7 +775,7 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
     const bool small = !own || i == j ||
                        (cabs2(W) <= 4e-8f * gap * gap && fabsf(gap) > 1e-5f * fmaxf(fabsf(di), fabsf(dj)));
     if (__all_sync(0xffffffffu, small)) {
-      // First-order step (as in lane_gevd): V <- V (I + X), X_ij = W_ij / (d_j - d_i);
+      // First-order step: V <- V (I + X), X_ij = W_ij / (d_j - d_i);
       // d_j += sum_p |W_pj|^2 / (d_j - d_p).
       const float2 X = (own && i != j) ? cscale(W, __fdividef(1.f, gap)) : make_float2(0.f, 0.f);
       float2 Vn = V;
