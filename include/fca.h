@@ -145,6 +145,32 @@ fca_status fca_loglik_bins(fca_state* s, double* out, int32_t* iters_out, void* 
  * none). */
 fca_status fca_sync_status(fca_state* s, void* cuda_stream);
 
+/* Precision of FastFCA's per-frequency generalised eigenproblem (Algorithm 1, step 8: the
+ * Cholesky factor of St2, the Hermitian Jacobi eigensolver of L^-1 St1 L^-H and Q = L^-H U of
+ * Eq. (GEVDeff5) and the Appendix), together with the cross-warp merge of the Gram sums that
+ * feed it (Eq. (updateStildeeff)).
+ *   FCA_GEVD_FP32:    both in FP32.
+ *   FCA_GEVD_FP64:    both in FP64 (the per-warp partial sums over frames stay FP32).
+ *   FCA_GEVD_REFINED: the merge in FP64; the Cholesky and Jacobi solve in FP32, then Q is
+ *                     refined in FP64 against the FP64 Grams until Q^H St2 Q = I and
+ *                     Q^H St1 Q is diagonal to second order in the FP32 solve's residuals
+ *                     (one Newton-type correction step, two after a poor start).
+ * In the FP64 and refined modes the next basis P Q is formed in FP64 before it is rounded for
+ * the bin pass. The bin pass is FP32 and the basis P, log-likelihood and log det S2 are kept
+ * in FP64 in every mode. Batches (fca_batch_*) run the FP32 mode. */
+enum { FCA_GEVD_FP32 = 0, FCA_GEVD_FP64 = 1, FCA_GEVD_REFINED = 2 };
+#define FCA_MAX_SWEEPS_LIMIT 1000
+
+/* Set the eigensolver precision (FCA_GEVD_FP32, _FP64 or _REFINED) and its cap on Jacobi sweeps
+ * per eigenproblem, 0 <= max_sweeps <= FCA_MAX_SWEEPS_LIMIT (a new state has the library
+ * default precision and a cap of 30). A solve that needs more sweeps stops, records
+ * FCA_ERR_EIG_NOCONV in the status word and leaves the state failed (the kernel returns; no
+ * wait). Applies to every later eigenproblem of the state: those of fca_em_fast,
+ * fca_em_fast_recover and fca_load. A state loaded since its last EM call solves the
+ * eigenproblem of S0 again, with these settings, at the next fca_em_fast. Host only;
+ * returns at once. */
+fca_status fca_set_eigensolver(fca_state* s, int32_t precision, int32_t max_sweeps);
+
 /* Release the state and all its device memory. Synchronises the device first. NULL is a
  * no-op. */
 void fca_free(fca_state* s);
@@ -157,6 +183,12 @@ fca_status fca_last_em_kernel_ms(fca_state* s, float* ms);
 
 /* Number of CUDA kernels this library has launched in this process (all states). */
 uint64_t fca_kernel_launches(void);
+
+/* Measured arithmetic peaks of the current device, for rating the kernels against (the paper
+ * has no counterpart): FP32 and FP64 fused multiply-add throughput in TFLOP/s (2 flops per
+ * FMA), from a kernel of independent FMA chains on every SM timed with CUDA events (about
+ * 0.3 s). Synchronous; allocates 64 bytes of device memory for the duration of the call. */
+fca_status fca_measure_peaks(double* fp32_tflops, double* fp64_tflops);
 
 /* Size of the fixed device scratch array behind fca_em_fast_noalloc (bytes). */
 #define FCA_NOALLOC_SCRATCH_BYTES (8u << 20)
@@ -183,9 +215,15 @@ uint64_t fca_kernel_launches(void);
  * log-determinants, current and previous) + 8 F max(L, 1) (per-bin log-likelihood) + 8 F N
  * (previous v) + 16 F M^2 + 4 F M (separation) bytes, plus 256; larger problems return
  * FCA_ERR_SCRATCH before any work is enqueued (M=4, F=513, N=1000, L=50 needs about 5 MB).
+ * The buffers are read and written in place, so they must be aligned: y_dev and S0_dev to
+ * 16 bytes, v0_dev, x1_dev, x2_dev and loglik_dev to 8, v_dev to 4 (cudaMalloc'd buffers
+ * and whole tensors are); otherwise FCA_ERR_ARG before any work is enqueued.
  * The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine). The
  * first call on a device looks up the array's device address there (cudaGetSymbolAddress,
- * with that device current) and should come before any stream capture on that device.
+ * with that device current); under lazy module loading (CUDA_MODULE_LOADING=LAZY, the
+ * default) that first lookup may also load the library's module and place the array, which
+ * allocates. Make one successful call on each device before entering a phase where
+ * allocation is not allowed, and before any stream capture on that device.
  * All calls share the array, so calls whose work overlaps on the GPU (other host threads,
  * other streams) race; the call therefore synchronises `cuda_stream` before returning, and
  * returns the first device-side error of this call (FCA_OK if none).

@@ -71,6 +71,8 @@ struct fca_state {
   int form;
   int prev_form;  // -1: no iteration run since the last load
   int failed;
+  int gevd_mode;   // FastFCA eigensolver and Gram merge precision (FCA_GEVD_*)
+  int max_sweeps;  // Jacobi sweep cap
 };
 
 namespace {
@@ -143,6 +145,8 @@ ParamArgs param_args(fca_state* s) {
   std::memset(&a, 0, sizeof(a));
   a.F = s->F;
   a.status = s->status;
+  a.max_sweeps = s->max_sweeps;
+  a.gevd_mode = s->gevd_mode;
   return a;
 }
 
@@ -192,6 +196,8 @@ fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
   const bool S_direct = on_dev && aligned(p->S0, 16);
   PrepareExtra ex;
   std::memset(&ex, 0, sizeof(ex));
+  ex.max_sweeps = s->max_sweeps;
+  ex.gevd_mode = s->gevd_mode;
   ex.P = s->P;
   ex.lam = s->lam;
   ex.logdetS2 = s->logdetS2;
@@ -242,6 +248,8 @@ fca_status fca_init(const fca_problem* p, void* stream, fca_state** out) {
   s->N_cap = p->N;
   s->storage = p->storage;
   s->device = dev;
+  s->gevd_mode = kDefaultGevdMode;
+  s->max_sweeps = kDefaultSweeps;
   s->FN = (size_t)p->F * p->N;
   s->MM = (size_t)p->M * p->M;
   const size_t F = s->F, FN = s->FN, MM = s->MM;
@@ -334,6 +342,8 @@ fca_status fca_em_fast(fca_state* s, int32_t iters, double* loglik_dev, void* st
   a.logdetS2_prev = s->logdetS2_prev;
   a.llf = s->llf;
   a.status = s->status;
+  a.max_sweeps = s->max_sweeps;
+  a.gevd_mode = s->gevd_mode;
   FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[0], st));
   FCA_CHECK_CUDA(counted(launch_fast_em(s->M, s->storage, a, st)));
   FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[1], st));
@@ -379,6 +389,8 @@ fca_status fca_em_fast_recover(fca_state* s, int32_t iters, double* loglik_dev, 
   a.lam_prev = s->lam_prev;
   a.logdetS2_prev = s->logdetS2_prev;
   a.status = s->status;
+  a.max_sweeps = s->max_sweeps;
+  a.gevd_mode = s->gevd_mode;
   FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[0], st));
   for (int l = 0; l < iters; ++l) {
     // One iteration (E-step, M-step in the transformed basis) with the parameters of
@@ -549,6 +561,18 @@ fca_status fca_sync_status(fca_state* s, void* stream) {
     s->failed = 1;
     return (fca_status)code;
   }
+  return FCA_OK;
+}
+
+fca_status fca_set_eigensolver(fca_state* s, int32_t precision, int32_t max_sweeps) {
+  if (!s || (precision != FCA_GEVD_FP32 && precision != FCA_GEVD_FP64 && precision != FCA_GEVD_REFINED) ||
+      max_sweeps < 0 || max_sweeps > FCA_MAX_SWEEPS_LIMIT)
+    return FCA_ERR_ARG;
+  s->gevd_mode = precision;
+  s->max_sweeps = max_sweeps;
+  // A state just loaded holds S0 and the eigenproblem of S0 solved with the old settings: the
+  // next fca_em_fast solves it again with these.
+  if (s->form == kFormSP) s->form = kFormS;
   return FCA_OK;
 }
 

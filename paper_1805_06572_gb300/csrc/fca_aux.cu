@@ -19,18 +19,6 @@ namespace fca {
 
 constexpr int kWarpsPerCta = 4;
 
-// 1/d for d > 0 by Newton-Raphson, r <- r + r (1 - d r), from the FP32 reciprocal of d: the
-// relative error squares each step, so two steps take the FP32 start (~2^-23) below FP64
-// rounding, at four FP64 FMAs instead of an FP64 division (several times their latency on
-// this GPU). Outside the FP32 normal range it divides.
-__device__ __forceinline__ double recip64(double d) {
-  if (!(d > 1e-36 && d < 1e36)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  r = fma(r, fma(-d, r, 1.0), r);
-  r = fma(r, fma(-d, r, 1.0), r);
-  return r;
-}
-
 // In-place inverse of the M x M matrix in aug[.][0..M) (aug[.][M..2M) must hold I); the
 // inverse ends in aug[.][M..2M). Returns false (uniformly) if a pivot is zero.
 template <int M>
@@ -88,14 +76,19 @@ __device__ bool warp_inverse64(double2 (*aug)[2 * kMaxM], int lane) {
   return true;
 }
 
+// FP64 input as the solver's complex type.
+template <typename G> __device__ __forceinline__ Cx<G> from_z(double2 a);
+template <> __device__ __forceinline__ float2 from_z<float>(double2 a) { return z2c(a); }
+template <> __device__ __forceinline__ double2 from_z<double>(double2 a) { return a; }
+
 // One warp: (P, Lambda, log det S2) of bin f from (S1, S2) (Eq. (GEVD)), by the solver the
-// EM kernel runs every iteration (register-resident for M <= 4, shared-memory otherwise);
-// P = Q, log det S2 = -log|det Q|^2. The bin's S is also copied to S_copy when that is set.
-// A failure leaves the bin's outputs unwritten and records its status.
-template <int M>
+// EM kernel runs every iteration (register-resident for M <= 4, shared-memory otherwise) in
+// precision G; P = Q, log det S2 = -log|det Q|^2. The bin's S is also copied to S_copy when
+// that is set. A failure leaves the bin's outputs unwritten and records its status.
+template <int M, typename G>
 __device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double2* P, double* lam,
-                         double* logdetS2, int* status, WarpLA& la, float* sig,
-                         float2 (*Q)[kMaxM], float2 (*U)[kMaxM], int lane) {
+                         double* logdetS2, int* status, WarpLAT<G>& la, G* sig,
+                         Cx<G> (*Q)[kMaxM], Cx<G> (*U)[kMaxM], int max_sweeps, int lane) {
   const size_t MM = (size_t)M * M;
   for (int e = lane; e < M * M; e += 32) {
     const double2 s1 = S[(size_t)f * MM + e], s2 = S[((size_t)F + f) * MM + e];
@@ -103,16 +96,16 @@ __device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double
       S_copy[(size_t)f * MM + e] = s1;
       S_copy[((size_t)F + f) * MM + e] = s2;
     }
-    la.A[e / M][e % M] = z2c(s1);
-    la.L[e / M][e % M] = z2c(s2);
+    la.A[e / M][e % M] = from_z<G>(s1);
+    la.L[e / M][e % M] = from_z<G>(s2);
   }
   __syncwarp();
-  float ldL = 0.f;
+  G ldL = G(0);
   int rc;
   if constexpr (M <= 4) {
-    rc = warp_gevd_reg<M>(la.A, la.L, sig, Q, U, &ldL, 2.0e-7f, 30, lane);
+    rc = warp_gevd_reg<M, G>(la.A, la.L, sig, Q, U, &ldL, Prec<G>::kTol, max_sweeps, lane);
   } else {
-    rc = warp_gevd_fast<M>(la, lane, sig, Q, U, &ldL);
+    rc = warp_gevd_fast<M, G>(la, lane, sig, Q, U, &ldL, max_sweeps);
   }
   __syncwarp();
   if (rc != kOk) {
@@ -125,15 +118,16 @@ __device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double
   if (lane == 0) logdetS2[f] = -ldQ;  // P = Q: log det S2 = -log|det P|^2
 }
 
-template <int M>
+template <int M, typename G>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) gevd_from_S_kernel(const ParamArgs a) {
-  __shared__ WarpLA la[kWarpsPerCta];
-  __shared__ float sig[kWarpsPerCta][kMaxM];
-  __shared__ float2 Q[kWarpsPerCta][kMaxM][kMaxM], U[kWarpsPerCta][kMaxM][kMaxM];
+  __shared__ WarpLAT<G> la[kWarpsPerCta];
+  __shared__ G sig[kWarpsPerCta][kMaxM];
+  __shared__ Cx<G> Q[kWarpsPerCta][kMaxM][kMaxM], U[kWarpsPerCta][kMaxM][kMaxM];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int f = blockIdx.x * kWarpsPerCta + w;
   if (f >= a.F) return;  // whole warp leaves together
-  gevd_bin<M>(a.S, nullptr, a.F, f, a.P, a.lam, a.logdetS2, a.status, la[w], sig[w], Q[w], U[w], lane);
+  gevd_bin<M, G>(a.S, nullptr, a.F, f, a.P, a.lam, a.logdetS2, a.status, la[w], sig[w], Q[w], U[w],
+                 a.max_sweeps, lane);
 }
 
 // mode 0: S_out = (P^-H Lam P^-1, P^-H P^-1); mode 1: separation prep.
@@ -271,7 +265,7 @@ __device__ float bin_power(const typename Elem<ST>::T* yf, typename Elem<ST>::T*
 // power, the initial v clamped to it, and checks that both are finite, all on warps 1..7
 // (synchronised among themselves by named barrier 1). Warp 0 meanwhile solves the bin's
 // generalised eigenproblem when extra.S is set (PrepareExtra).
-template <int M, int ST, bool kX>
+template <int M, int ST, bool kX, typename G = float>
 __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void* y, const float* ginv,
                                                       const double* v0, float* v, float* vfloor,
                                                       int* status, const BinDesc* bins,
@@ -280,9 +274,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
   constexpr int kStreamThreads = 224;
   __shared__ double part[8];
   __shared__ float vf_s;
-  __shared__ WarpLA la;  // used (and kept) only by the kX variants
-  __shared__ float sig[kMaxM];
-  __shared__ float2 Qs[kMaxM][kMaxM], Us[kMaxM][kMaxM];
+  __shared__ WarpLAT<G> la;  // used (and kept) only by the kX variants
+  __shared__ G sig[kMaxM];
+  __shared__ Cx<G> Qs[kMaxM][kMaxM], Us[kMaxM][kMaxM];
   const int tid = threadIdx.x;
   int f, N;
   size_t yoff, voff[2];
@@ -302,7 +296,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
   }
   int bad = 0;
   if (tid < 32) {
-    if (kX && ex.S) gevd_bin<M>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, la, sig, Qs, Us, tid);
+    if (kX && ex.S)
+      gevd_bin<M, G>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, la, sig, Qs, Us,
+                     ex.max_sweeps, tid);
   } else {
     const int t = tid - 32;
     E* yc = (kX && ex.y_copy) ? reinterpret_cast<E*>(ex.y_copy) + yoff : nullptr;
@@ -402,7 +398,10 @@ __global__ void invert_scale_kernel(int F, const float* g, float* ginv) {
 cudaError_t launch_gevd_from_S(int M, const ParamArgs& a, cudaStream_t st) {
   const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid <= 0) return cudaSuccess;
-  FCA_DISPATCH_M(M, (gevd_from_S_kernel<kM><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
+  if (a.gevd_mode) {
+    FCA_DISPATCH_M(M, (gevd_from_S_kernel<kM, double><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
+  }
+  FCA_DISPATCH_M(M, (gevd_from_S_kernel<kM, float><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
 }
 
 cudaError_t launch_S_from_P(int M, const ParamArgs& a, cudaStream_t st) {
@@ -423,6 +422,13 @@ cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, cons
   if (F <= 0) return cudaSuccess;
   if (extra && bins) return cudaErrorInvalidValue;  // the fused work assumes the [F][N][M] layout
   const PrepareExtra ex = extra ? *extra : PrepareExtra{};
+  if (extra && ex.gevd_mode) {
+    if (storage) {
+      FCA_DISPATCH_M(M, (prepare_kernel<kM, 1, true, double><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
+    } else {
+      FCA_DISPATCH_M(M, (prepare_kernel<kM, 0, true, double><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
+    }
+  }
   if (extra) {
     if (storage) {
       FCA_DISPATCH_M(M, (prepare_kernel<kM, 1, true><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())

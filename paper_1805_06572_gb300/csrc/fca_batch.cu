@@ -213,6 +213,8 @@ FastEmArgs fast_args(fca_batch* b, BatchClass& c, int iters, const BinDesc* bins
   a.logdetS2_prev = c.ldet_prev;
   a.llf = c.llf;
   a.status = b->status;
+  a.max_sweeps = kDefaultSweeps;
+  a.gevd_mode = 0;  // the batch kernels run the FP32 eigensolver
   return a;
 }
 
@@ -221,6 +223,8 @@ ParamArgs param_args(fca_batch* b, BatchClass& c) {
   std::memset(&a, 0, sizeof(a));
   a.F = c.nbins;
   a.status = b->status;
+  a.max_sweeps = kDefaultSweeps;
+  a.gevd_mode = 0;
   return a;
 }
 

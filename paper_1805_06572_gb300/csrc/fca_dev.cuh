@@ -247,40 +247,138 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// ------------------------------------------------------- precision of the per-bin solver
+// The per-bin linear algebra below runs in FP32 (T = float, complex float2) or FP64 (T =
+// double, complex double2), chosen at compile time; the formulas are the same.
+template <typename T> struct CxT;
+template <> struct CxT<float> { typedef float2 type; };
+template <> struct CxT<double> { typedef double2 type; };
+template <typename T> using Cx = typename CxT<T>::type;
+
+// complex128 versions of the complex64 helpers above (same formulas, FP64 fused multiply-adds)
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ double2 ccmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double2 c2z(double2 a) { return a; }
+
+template <typename T> __device__ __forceinline__ Cx<T> mkc(T re, T im);
+template <> __device__ __forceinline__ float2 mkc<float>(float re, float im) { return make_float2(re, im); }
+template <> __device__ __forceinline__ double2 mkc<double>(double re, double im) { return make_double2(re, im); }
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float absT(float a) { return fabsf(a); }
+__device__ __forceinline__ double absT(double a) { return fabs(a); }
+__device__ __forceinline__ float maxT(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double maxT(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float copysignT(float a, float b) { return copysignf(a, b); }
+__device__ __forceinline__ double copysignT(double a, double b) { return copysign(a, b); }
+__device__ __forceinline__ float logT(float a) { return logf(a); }
+__device__ __forceinline__ double logT(double a) { return log(a); }
+
+// 1/d for d > 0 in FP64 by Newton-Raphson, r <- r + r (1 - d r), from the FP32 reciprocal of
+// d: the relative error squares each step, so two steps take the FP32 start (~2^-23) below
+// FP64 rounding, at four FP64 FMAs instead of an FP64 division (several times their latency
+// on this GPU). Outside the FP32 normal range it divides.
+__device__ __forceinline__ double recip64(double d) {
+  if (!(d > 1e-36 && d < 1e36)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
+// 1/sqrt(x) for x > 0: the hardware approximation refined by Newton's iteration
+// r <- r (3 - x r^2) / 2, once in FP32; in FP64 twice from the FP32 value (the relative error
+// roughly squares each step: ~2^-22 -> 2^-43 -> below FP64 rounding), dividing outside the
+// FP32 normal range.
+__device__ __forceinline__ float rsq_nr(float x) {
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+__device__ __forceinline__ double rsq_nr(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+  double r = (double)rsqrtf((float)x);
+  r = r * fma(-0.5 * x * r, r, 1.5);
+  return r * fma(-0.5 * x * r, r, 1.5);
+}
+// sqrt(h) for h >= 1 (the Jacobi angle): h times the plain FP32 approximation of 1/sqrt(h);
+// in FP64 from the refined one.
+__device__ __forceinline__ float sqrt_h(float h) { return h * rsqrtf(h); }
+__device__ __forceinline__ double sqrt_h(double h) { return h * rsq_nr(h); }
+// 1/x (x != 0): the fast FP32 division; in FP64 the Newton reciprocal.
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double rcp_fast(double x) { return recip64(x); }
+
+// Thresholds of the eigensolver per precision.
+//   kHuge:   finite-value guard for pivots and eigenvalues;
+//   kTiny2:  |a_pq|^2 below which an off-diagonal entry counts as zero;
+//   kTol:    a pivot with |a_pq| <= kTol sqrt(|a_pp a_qq|) is not rotated;
+//   kBig2:   a sweep whose pivots all had |a_pq|^2 <= kBig2 |a_pp a_qq| leaves off-diagonal
+//            entries of order kBig2 relative (quadratic convergence): the solve ends;
+//   kFirst2, kGap: the first-order finish runs once every |a_ij|^2 <= kFirst2 (a_jj - a_ii)^2
+//            and every gap exceeds kGap of the larger eigenvalue; its error is then of order
+//            kFirst2 relative.
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+  static constexpr float kHuge = 3.0e38f, kTiny2 = 1e-36f, kTol = 2.0e-7f, kBig2 = 1e-8f,
+                         kFirst2 = 4e-8f, kGap = 1e-5f;
+};
+template <> struct Prec<double> {
+  static constexpr double kHuge = 1e300, kTiny2 = 1e-300, kTol = 1e-15, kBig2 = 1e-16,
+                          kFirst2 = 1e-16, kGap = 1e-8;
+};
+
 // --------------------------------------------------- warp-level dense Hermitian algebra
 // Matrices are row-major with leading dimension kMaxM, in shared memory. Every function is
 // called by all 32 lanes of one warp and ends with __syncwarp().
-struct WarpLA {
-  float2 A[kMaxM][kMaxM];   // work matrix (eigenproblem)
-  float2 L[kMaxM][kMaxM];   // Cholesky factor (lower triangle); L^-1 in the fast solver
-  float2 Z[kMaxM][kMaxM];   // temporary
-  float2 V[kMaxM][kMaxM];   // eigenvectors / result
-  float2 A2[kMaxM][kMaxM];  // ping-pong partners of A and V (fast solver)
-  float2 V2[kMaxM][kMaxM];
-  float invd[kMaxM];        // 1 / L_ii
-  float2 jself[kMaxM + 1];  // Jacobi: J_xx for every index x
-  float2 joth[kMaxM + 1];   // Jacobi: J_{partner(x), x}
+template <typename T>
+struct WarpLAT {
+  using C = Cx<T>;
+  C A[kMaxM][kMaxM];   // work matrix (eigenproblem)
+  C L[kMaxM][kMaxM];   // Cholesky factor (lower triangle); L^-1 in the fast solver
+  C Z[kMaxM][kMaxM];   // temporary
+  C V[kMaxM][kMaxM];   // eigenvectors / result
+  C A2[kMaxM][kMaxM];  // ping-pong partners of A and V (fast solver)
+  C V2[kMaxM][kMaxM];
+  T invd[kMaxM];       // 1 / L_ii
+  C jself[kMaxM + 1];  // Jacobi: J_xx for every index x
+  C joth[kMaxM + 1];   // Jacobi: J_{partner(x), x}
   int partner[kMaxM + 1];
 };
+using WarpLA = WarpLAT<float>;
 
 // In-place Cholesky B = L L^H of the Hermitian positive definite matrix in la.L (the lower
 // triangle is read and overwritten). Returns false (uniformly across the warp) if a pivot is
 // not positive and finite.
-template <int M>
-__device__ bool warp_cholesky(WarpLA& la, int lane) {
+template <int M, typename T>
+__device__ bool warp_cholesky(WarpLAT<T>& la, int lane) {
   for (int k = 0; k < M; ++k) {
     __syncwarp();
-    const float bkk = la.L[k][k].x;
-    if (!(bkk > 0.f) || !(bkk < 3.0e38f)) {
+    const T bkk = la.L[k][k].x;
+    if (!(bkk > T(0)) || !(bkk < Prec<T>::kHuge)) {
       __syncwarp();
       return false;
     }
-    float il = rsqrtf(bkk);
-    il = il * fmaf(-0.5f * bkk * il, il, 1.5f);  // Newton step: 1/sqrt(bkk) to rounding
-    const float lkk = bkk * il;
+    const T il = rsq_nr(bkk);  // 1/sqrt(bkk) to rounding
+    const T lkk = bkk * il;
     __syncwarp();
     if (lane == k) {
-      la.L[k][k] = make_float2(lkk, 0.f);
+      la.L[k][k] = mkc<T>(lkk, T(0));
       la.invd[k] = il;
     } else if (lane > k && lane < M) {
       la.L[lane][k] = cscale(la.L[lane][k], il);
@@ -299,8 +397,8 @@ __device__ bool warp_cholesky(WarpLA& la, int lane) {
 // Generalised eigenproblem of the Hermitian pencil (A, B), B positive definite, given in
 // la.A (A) and la.L (B): Cholesky B = L L^H, W = L^-1 A L^-H = U Sig U^H (Jacobi),
 // Q = L^-H U, so that Q^H B Q = I and Q^H A Q = Sig (Eq. (GEVDeff5)). log|det Q|^2 =
-// 2 sum_i log(1/L_ii) + log|det U|^2, where the FP32 rotations leave U unitary only to
-// rounding, so log|det U|^2 = log det(U^H U) = ||U||_F^2 - M to first order in U^H U - I.
+// 2 sum_i log(1/L_ii) + log|det U|^2, where the rotations leave U unitary only to rounding,
+// so log|det U|^2 = log det(U^H U) = ||U||_F^2 - M to first order in U^H U - I.
 // Arranged for a short dependency chain:
 // one lane factors B = L L^H and inverts L in registers (no warp synchronisation inside the
 // recurrences), the congruence W = L^-1 A L^-H and Q = L^-H U are lane-parallel products,
@@ -309,40 +407,40 @@ __device__ bool warp_cholesky(WarpLA& la, int lane) {
 
 // Lane 0: B (lower triangle of la.L) = L L^H; writes L^-1 (lower, zero above) over la.L and
 // returns log|det L^-H|^2 = 2 sum_i log(1/L_ii). Result is valid on lane 0 only; *ok too.
-template <int M>
-__device__ float lane_cholesky_inverse(WarpLA& la, bool* ok) {
-  float2 L[M][M];
-  float id[M];
+template <int M, typename T>
+__device__ T lane_cholesky_inverse(WarpLAT<T>& la, bool* ok) {
+  using C = Cx<T>;
+  C L[M][M];
+  T id[M];
   bool good = true;
 #pragma unroll
   for (int j = 0; j < M; ++j) {
 #pragma unroll
     for (int i = j; i < M; ++i) {
-      float2 s = la.L[i][j];
+      C s = la.L[i][j];
 #pragma unroll
       for (int k = 0; k < j; ++k) s = csub(s, cmulc(L[i][k], L[j][k]));
       if (i == j) {
-        const float piv = s.x;
-        good = good && (piv > 0.f) && (piv < 3.0e38f);
-        float il = rsqrtf(piv);
-        il = il * fmaf(-0.5f * piv * il, il, 1.5f);  // Newton step: 1/sqrt to rounding
+        const T piv = s.x;
+        good = good && (piv > T(0)) && (piv < Prec<T>::kHuge);
+        const T il = rsq_nr(piv);  // 1/sqrt to rounding
         id[j] = il;
-        L[j][j] = make_float2(piv * il, 0.f);
+        L[j][j] = mkc<T>(piv * il, T(0));
       } else {
         L[i][j] = cscale(s, id[j]);
       }
     }
   }
   // L^-1: (L^-1)_ii = id_i; (L^-1)_ij = -id_i sum_{k=j}^{i-1} L_ik (L^-1)_kj for i > j.
-  float2 Li[M][M];
-  float ld = 0.f;
+  C Li[M][M];
+  T ld = T(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    Li[j][j] = make_float2(id[j], 0.f);
-    ld += 2.f * logf(id[j]);
+    Li[j][j] = mkc<T>(id[j], T(0));
+    ld += T(2) * logT(id[j]);
 #pragma unroll
     for (int i = j + 1; i < M; ++i) {
-      float2 s = make_float2(0.f, 0.f);
+      C s = mkc<T>(T(0), T(0));
 #pragma unroll
       for (int k = j; k < i; ++k) s = cfma(L[i][k], Li[k][j], s);
       Li[i][j] = cscale(s, -id[i]);
@@ -352,22 +450,23 @@ __device__ float lane_cholesky_inverse(WarpLA& la, bool* ok) {
   for (int i = 0; i < M; ++i) {
     la.invd[i] = id[i];
 #pragma unroll
-    for (int j = 0; j < M; ++j) la.L[i][j] = (j <= i) ? Li[i][j] : make_float2(0.f, 0.f);
+    for (int j = 0; j < M; ++j) la.L[i][j] = (j <= i) ? Li[i][j] : mkc<T>(T(0), T(0));
   }
   *ok = good;
   return ld;
 }
 
 // la.A <- W = Li A Li^H (Li = la.L, lower triangular), Hermitian by construction.
-template <int M>
-__device__ void warp_congruence_products(WarpLA& la, int lane) {
+template <int M, typename T>
+__device__ void warp_congruence_products(WarpLAT<T>& la, int lane) {
+  using C = Cx<T>;
   constexpr int kPer = (M * M + 31) / 32;
 #pragma unroll
   for (int t = 0; t < kPer; ++t) {  // Z = A Li^H:  Z_ij = sum_{k<=j} A_ik conj(Li_jk)
     const int e = lane + 32 * t;
     if (e < M * M) {
       const int i = e / M, j = e % M;
-      float2 s = make_float2(0.f, 0.f);
+      C s = mkc<T>(T(0), T(0));
 #pragma unroll
       for (int k = 0; k < M; ++k)
         if (k <= j) s = cadd(s, cmulc(la.A[i][k], la.L[j][k]));
@@ -387,12 +486,12 @@ __device__ void warp_congruence_products(WarpLA& la, int lane) {
         ++i;
       }
       const int j = i + r;
-      float2 s = make_float2(0.f, 0.f);
+      C s = mkc<T>(T(0), T(0));
 #pragma unroll
       for (int k = 0; k < M; ++k)
         if (k <= i) s = cfma(la.L[i][k], la.Z[k][j], s);
       if (i == j) {
-        la.A[i][i] = make_float2(s.x, 0.f);
+        la.A[i][i] = mkc<T>(s.x, T(0));
       } else {
         la.A[i][j] = s;
         la.A[j][i] = cconj(s);
@@ -409,22 +508,24 @@ __device__ void warp_congruence_products(WarpLA& la, int lane) {
 // J_qp = -s conj(e), J_qq = c conj(e) zeroes a_pq: A <- J^H A J, V <- V J. Pivots below
 // tol relative to sqrt(|a_pp a_qq|) are skipped. Each round reads A/V from one buffer and
 // writes the other; on return the current buffers are la.A / la.V (an even number of swaps is
-// enforced by a final copy when needed).
-template <int M>
-__device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
+// enforced by a final copy when needed). Returns the sweeps taken, or -1 past max_sweeps.
+template <int M, typename T>
+__device__ int warp_jacobi_pp(WarpLAT<T>& la, int lane, T tol, int max_sweeps) {
+  using C = Cx<T>;
+  using PT = Prec<T>;
   constexpr int n = M + (M & 1);
   constexpr int kPer = (M * M + 31) / 32;
   for (int e = lane; e < M * M; e += 32) {
     const int i = e / M, j = e - (e / M) * M;
-    la.V[i][j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    la.V[i][j] = mkc<T>(i == j ? T(1) : T(0), T(0));
   }
   __syncwarp();
   if (M == 1) return 0;
-  const float tol2 = tol * tol;
-  float2(*Ac)[kMaxM] = la.A;
-  float2(*Vc)[kMaxM] = la.V;
-  float2(*An)[kMaxM] = la.A2;
-  float2(*Vn)[kMaxM] = la.V2;
+  const T tol2 = tol * tol;
+  C(*Ac)[kMaxM] = la.A;
+  C(*Vc)[kMaxM] = la.V;
+  C(*An)[kMaxM] = la.A2;
+  C(*Vn)[kMaxM] = la.V2;
   int result = -1;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int rotated = 0, big = 0;
@@ -434,36 +535,34 @@ __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
         const int a = (k == 0) ? r : (r + k) % (n - 1);
         const int b = (k == 0) ? n - 1 : (r - k + (n - 1)) % (n - 1);
         const int p = min(a, b), q = max(a, b);
-        float c = 1.f, s = 0.f;
-        float2 e = make_float2(1.f, 0.f);
+        T c = T(1), s = T(0);
+        C e = mkc<T>(T(1), T(0));
         if (q < M) {
-          const float app = Ac[p][p].x, aqq = Ac[q][q].x;
-          const float2 apq = Ac[p][q];
-          const float r2 = cabs2(apq);
-          const float den = fabsf(app * aqq);
-          if (r2 > tol2 * den && r2 > 1e-36f) {
-            big |= (r2 > 1e-8f * den);
-            float ir = rsqrtf(r2);
-            ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);   // 1 / |a_pq|, Newton-refined
-            const float tau = 0.5f * (aqq - app) * ir;
-            const float h = fmaf(tau, tau, 1.f);
-            const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
-            const float g = fmaf(t, t, 1.f);
-            c = rsqrtf(g);
-            c = c * fmaf(-0.5f * g * c, c, 1.5f);         // Newton-refined: c^2 + s^2 = 1
+          const T app = Ac[p][p].x, aqq = Ac[q][q].x;
+          const C apq = Ac[p][q];
+          const T r2 = cabs2(apq);
+          const T den = absT(app * aqq);
+          if (r2 > tol2 * den && r2 > PT::kTiny2) {
+            big |= (r2 > PT::kBig2 * den);
+            const T ir = rsq_nr(r2);  // 1 / |a_pq|
+            const T tau = T(0.5) * (aqq - app) * ir;
+            const T h = fmaT(tau, tau, T(1));
+            const T t = copysignT(rcp_fast(absT(tau) + sqrt_h(h)), tau);
+            const T g = fmaT(t, t, T(1));
+            c = rsq_nr(g);  // refined: c^2 + s^2 = 1
             s = t * c;
             e = cscale(apq, ir);
             rotated = 1;
           }
-          la.jself[p] = make_float2(c, 0.f);
+          la.jself[p] = mkc<T>(c, T(0));
           la.joth[p] = cscale(cconj(e), -s);
           la.partner[p] = q;
           la.jself[q] = cscale(cconj(e), c);
-          la.joth[q] = make_float2(s, 0.f);
+          la.joth[q] = mkc<T>(s, T(0));
           la.partner[q] = p;
         } else {
-          la.jself[p] = make_float2(1.f, 0.f);
-          la.joth[p] = make_float2(0.f, 0.f);
+          la.jself[p] = mkc<T>(T(1), T(0));
+          la.joth[p] = mkc<T>(T(0), T(0));
           la.partner[p] = p;
         }
       }
@@ -474,18 +573,18 @@ __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
         if (e < M * M) {
           const int i = e / M, l = e - (e / M) * M;
           const int ip = la.partner[i], lp = la.partner[l];
-          const float2 Ji = la.jself[i], Jo_i = la.joth[i], Jl = la.jself[l], Jo_l = la.joth[l];
-          const float2 r0 = cfma(Ac[i][lp], Jo_l, cmul(Ac[i][l], Jl));
-          const float2 r1 = cfma(Ac[ip][lp], Jo_l, cmul(Ac[ip][l], Jl));
-          float2 v = cadd(ccmul(Ji, r0), ccmul(Jo_i, r1));
-          if (i == l) v.y = 0.f;
-          else if (ip == l) v = make_float2(0.f, 0.f);  // the pivot pair
+          const C Ji = la.jself[i], Jo_i = la.joth[i], Jl = la.jself[l], Jo_l = la.joth[l];
+          const C r0 = cfma(Ac[i][lp], Jo_l, cmul(Ac[i][l], Jl));
+          const C r1 = cfma(Ac[ip][lp], Jo_l, cmul(Ac[ip][l], Jl));
+          C v = cadd(ccmul(Ji, r0), ccmul(Jo_i, r1));
+          if (i == l) v.y = T(0);
+          else if (ip == l) v = mkc<T>(T(0), T(0));  // the pivot pair
           An[i][l] = v;
           Vn[i][l] = cfma(Vc[i][lp], Jo_l, cmul(Vc[i][l], Jl));
         }
       }
       __syncwarp();
-      float2(*t0)[kMaxM] = Ac;
+      C(*t0)[kMaxM] = Ac;
       Ac = An;
       An = t0;
       t0 = Vc;
@@ -496,7 +595,7 @@ __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
       result = sweep + 1;
       break;
     }
-    // First-order finish (as in warp_gevd_reg) once every off-diagonal entry is below 2e-4 of
+    // First-order finish (as in warp_gevd_reg) once every off-diagonal entry is small against
     // its eigenvalue gap: V <- V (I + X), X_ij = A_ij / (d_j - d_i) (skew-Hermitian, written
     // into the free ping-pong buffer), d_j += sum_p |A_pj|^2 / (d_j - d_p).
     // (Every gap must also stand clear of the eigenvalues' size: degenerate pairs take
@@ -505,34 +604,34 @@ __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
     for (int e = lane; e < M * M; e += 32) {
       const int i = e / M, j = e % M;
       if (i != j) {
-        const float gap = Ac[j][j].x - Ac[i][i].x;
-        const float scale = fmaxf(fabsf(Ac[i][i].x), fabsf(Ac[j][j].x));
-        small &= (cabs2(Ac[i][j]) <= 4e-8f * gap * gap && fabsf(gap) > 1e-5f * scale) ? 1 : 0;
+        const T gap = Ac[j][j].x - Ac[i][i].x;
+        const T scale = maxT(absT(Ac[i][i].x), absT(Ac[j][j].x));
+        small &= (cabs2(Ac[i][j]) <= PT::kFirst2 * gap * gap && absT(gap) > PT::kGap * scale) ? 1 : 0;
       }
     }
     if (__all_sync(0xffffffffu, small)) {
       for (int e = lane; e < M * M; e += 32) {
         const int i = e / M, j = e % M;
-        An[i][j] = (i != j) ? cscale(Ac[i][j], __fdividef(1.f, Ac[j][j].x - Ac[i][i].x))
-                            : make_float2(0.f, 0.f);
+        An[i][j] = (i != j) ? cscale(Ac[i][j], rcp_fast(Ac[j][j].x - Ac[i][i].x))
+                            : mkc<T>(T(0), T(0));
       }
       __syncwarp();
-      float2 nv[kPer];
-      float corr[kPer];
+      C nv[kPer];
+      T corr[kPer];
 #pragma unroll
       for (int t = 0; t < kPer; ++t) {
         const int e = lane + 32 * t;
-        corr[t] = 0.f;
+        corr[t] = T(0);
         if (e < M * M) {
           const int i = e / M, j = e % M;
-          float2 acc = Vc[i][j];
+          C acc = Vc[i][j];
 #pragma unroll
           for (int m = 0; m < M; ++m) acc = cfma(Vc[i][m], An[m][j], acc);
           nv[t] = acc;
           if (i == j) {
 #pragma unroll
             for (int p2 = 0; p2 < M; ++p2)
-              corr[t] = fmaf(Ac[p2][j].x, An[p2][j].x, fmaf(Ac[p2][j].y, An[p2][j].y, corr[t]));
+              corr[t] = fmaT(Ac[p2][j].x, An[p2][j].x, fmaT(Ac[p2][j].y, An[p2][j].y, corr[t]));
           }
         }
       }
@@ -564,20 +663,21 @@ __device__ int warp_jacobi_pp(WarpLA& la, int lane, float tol, int max_sweeps) {
 
 // Low-latency generalised eigenproblem of (A, B) in (la.A, la.L): writes Q = L^-H U into
 // Qout and U into Uout ([kMaxM][kMaxM]), Sig into sig, and returns 2 sum_i log(1/L_ii) in
-// *ldL. log|det Q|^2 = *ldL + log|det U|^2, where the FP32 rotations leave U unitary only to
+// *ldL. log|det Q|^2 = *ldL + log|det U|^2, where the rotations leave U unitary only to
 // rounding: log|det U|^2 = ||U||_F^2 - M to first order, which the caller sums in FP64 from
 // Uout (unitarity_defect). Returns a device status code.
-template <int M>
-__device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[kMaxM],
-                              float2 (*Uout)[kMaxM], float* ldL) {
+template <int M, typename T>
+__device__ int warp_gevd_fast(WarpLAT<T>& la, int lane, T* sig, Cx<T> (*Qout)[kMaxM],
+                              Cx<T> (*Uout)[kMaxM], T* ldL, int max_sweeps) {
+  using C = Cx<T>;
   bool ok = true;
-  float ld = 0.f;
+  T ld = T(0);
   if (lane == 0) ld = lane_cholesky_inverse<M>(la, &ok);
   ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
   __syncwarp();
   if (!ok) return kErrNotPD;
   warp_congruence_products<M>(la, lane);
-  const int sw = warp_jacobi_pp<M>(la, lane, 2.0e-7f, 30);
+  const int sw = warp_jacobi_pp<M>(la, lane, Prec<T>::kTol, max_sweeps);
   if (sw < 0) return kErrEigNoConv;
   if (lane < M) sig[lane] = la.A[lane][lane].x;
   constexpr int kPer = (M * M + 31) / 32;
@@ -586,7 +686,7 @@ __device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[k
     const int e = lane + 32 * t;
     if (e < M * M) {
       const int i = e / M, j = e % M;
-      float2 s = make_float2(0.f, 0.f);
+      C s = mkc<T>(T(0), T(0));
 #pragma unroll
       for (int k = 0; k < M; ++k)
         if (k >= i) s = cadd(s, ccmul(la.L[k][i], la.V[k][j]));
@@ -598,8 +698,8 @@ __device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[k
   __syncwarp();
   *ldL = ld;
   for (int i = 0; i < M; ++i) {
-    const float sv = sig[i];
-    if (!(sv > 0.f) || !(sv < 3.0e38f)) return kErrNotPD;
+    const T sv = sig[i];
+    if (!(sv > T(0)) || !(sv < Prec<T>::kHuge)) return kErrNotPD;
   }
   return kOk;
 }
@@ -607,6 +707,9 @@ __device__ int warp_gevd_fast(WarpLA& la, int lane, float* sig, float2 (*Qout)[k
 // ------------------------------------------------------ register-resident solver, M <= 4
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
 // Partner of index x in round r of the round-robin pairing of n positions (n even): position
@@ -626,37 +729,38 @@ __device__ __forceinline__ int rr_partner(int x, int r, int n) {
 // recurrences) and writes L^-1 over B. Each Jacobi round (the rotation of warp_jacobi_pp)
 // rotates the disjoint round-robin pairs at once (every lane computes the angle of its row's
 // pair; the column's comes by shuffle). Sweeps stop when a sweep rotated nothing or no pivot
-// exceeded 1e-4 of sqrt(|a_pp a_qq|), or with the first-order step once every off-diagonal
-// entry is below 2e-4 of its eigenvalue gap. Called by all 32 lanes.
-template <int M>
-__device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float* sig,
-                             float2 (*Qout)[kMaxM], float2 (*Uout)[kMaxM], float* ldL, float tol,
+// was large (Prec<T>::kBig2), or with the first-order step once every off-diagonal entry is
+// small against its eigenvalue gap (Prec<T>::kFirst2). Called by all 32 lanes.
+template <int M, typename T>
+__device__ int warp_gevd_reg(const Cx<T> (*A)[kMaxM], Cx<T> (*B)[kMaxM], T* sig,
+                             Cx<T> (*Qout)[kMaxM], Cx<T> (*Uout)[kMaxM], T* ldL, T tol,
                              int max_sweeps, int lane) {
   static_assert(M >= 1 && M <= 4, "one entry per lane: M*M <= 32 (and sized for M <= 4)");
+  using C = Cx<T>;
+  using PT = Prec<T>;
   constexpr int MM = M * M;
   constexpr int n = M + (M & 1);
   const bool own = lane < MM;
   const int i = own ? lane / M : 0, j = own ? lane % M : 0;
   // 1. Cholesky and L^-1 on lane 0.
   int ok = 1;
-  float ld = 0.f;
+  T ld = T(0);
   if (lane == 0) {
-    float2 L[M][M];
-    float id[M];
+    C L[M][M];
+    T id[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
 #pragma unroll
       for (int r = c; r < M; ++r) {
-        float2 sv = B[r][c];
+        C sv = B[r][c];
 #pragma unroll
         for (int k = 0; k < c; ++k) sv = csub(sv, cmulc(L[r][k], L[c][k]));
         if (r == c) {
-          const float piv = sv.x;
-          ok = ok && (piv > 0.f) && (piv < 3.0e38f);
-          float il = rsqrtf(piv);
-          il = il * fmaf(-0.5f * piv * il, il, 1.5f);  // Newton step: 1/sqrt to rounding
+          const T piv = sv.x;
+          ok = ok && (piv > T(0)) && (piv < PT::kHuge);
+          const T il = rsq_nr(piv);  // 1/sqrt to rounding
           id[c] = il;
-          L[c][c] = make_float2(piv * il, 0.f);
+          L[c][c] = mkc<T>(piv * il, T(0));
         } else {
           L[r][c] = cscale(sv, id[c]);
         }
@@ -664,15 +768,15 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
     }
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-      B[c][c] = make_float2(id[c], 0.f);
-      ld += 2.f * logf(id[c]);
+      B[c][c] = mkc<T>(id[c], T(0));
+      ld += T(2) * logT(id[c]);
 #pragma unroll
       for (int r = c + 1; r < M; ++r) {
-        float2 sv = make_float2(0.f, 0.f);
+        C sv = mkc<T>(T(0), T(0));
 #pragma unroll
-        for (int k = c; k < r; ++k) sv = cfma(L[r][k], (k == c) ? make_float2(id[c], 0.f) : B[k][c], sv);
+        for (int k = c; k < r; ++k) sv = cfma(L[r][k], (k == c) ? mkc<T>(id[c], T(0)) : B[k][c], sv);
         B[r][c] = cscale(sv, -id[r]);
-        B[c][r] = make_float2(0.f, 0.f);
+        B[c][r] = mkc<T>(T(0), T(0));
       }
     }
   }
@@ -681,24 +785,24 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
   __syncwarp();
   if (!ok) return kErrNotPD;
   // 2. W = Li A Li^H: T = A Li^H (T_ij = sum_{k<=j} A_ik conj(Li_jk)), W_ij = sum_{k<=i} Li_ik T_kj.
-  float2 T = make_float2(0.f, 0.f);
+  C Tm = mkc<T>(T(0), T(0));
 #pragma unroll
   for (int k = 0; k < M; ++k)
-    if (k <= j) T = cadd(T, cmulc(A[i][k], B[j][k]));
-  float2 W = make_float2(0.f, 0.f);
+    if (k <= j) Tm = cadd(Tm, cmulc(A[i][k], B[j][k]));
+  C W = mkc<T>(T(0), T(0));
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const float2 tk = shfl2(T, own ? k * M + j : lane);
+    const C tk = shfl2(Tm, own ? k * M + j : lane);
     if (k <= i) W = cfma(B[i][k], tk, W);
   }
   {  // exactly Hermitian: the lower triangle mirrors the upper one
-    const float2 wt = shfl2(W, own ? j * M + i : lane);
+    const C wt = shfl2(W, own ? j * M + i : lane);
     if (i > j) W = cconj(wt);
-    if (i == j) W.y = 0.f;
+    if (i == j) W.y = T(0);
   }
-  float2 V = make_float2(i == j ? 1.f : 0.f, 0.f);
+  C V = mkc<T>(i == j ? T(1) : T(0), T(0));
   // 3. Jacobi sweeps.
-  const float tol2 = tol * tol;
+  const T tol2 = tol * tol;
   int sweeps = (M == 1) ? 0 : -1;
   for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
     int rotated = 0, big = 0;
@@ -707,57 +811,55 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
       const int pi = rr_partner(i, r, n), pj = rr_partner(j, r, n);
       const int p = min(i, pi), q = max(i, pi);
       const bool valid = own && q < M;
-      const float app = __shfl_sync(0xffffffffu, W.x, valid ? p * M + p : lane);
-      const float aqq = __shfl_sync(0xffffffffu, W.x, valid ? q * M + q : lane);
-      const float2 apq = shfl2(W, valid ? p * M + q : lane);
-      float2 Jii = make_float2(1.f, 0.f), Joi = make_float2(0.f, 0.f);  // J_{i i}, J_{i' i}
+      const T app = __shfl_sync(0xffffffffu, W.x, valid ? p * M + p : lane);
+      const T aqq = __shfl_sync(0xffffffffu, W.x, valid ? q * M + q : lane);
+      const C apq = shfl2(W, valid ? p * M + q : lane);
+      C Jii = mkc<T>(T(1), T(0)), Joi = mkc<T>(T(0), T(0));  // J_{i i}, J_{i' i}
       bool act = false;
       if (valid) {
-        const float r2 = cabs2(apq);
-        const float den = fabsf(app * aqq);
-        if (r2 > tol2 * den && r2 > 1e-36f) {
+        const T r2 = cabs2(apq);
+        const T den = absT(app * aqq);
+        if (r2 > tol2 * den && r2 > PT::kTiny2) {
           act = true;
-          big |= (r2 > 1e-8f * den);
-          float ir = rsqrtf(r2);
-          ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
-          const float tau = 0.5f * (aqq - app) * ir;
-          const float h = fmaf(tau, tau, 1.f);
-          const float t = copysignf(__fdividef(1.f, fabsf(tau) + h * rsqrtf(h)), tau);
-          const float g = fmaf(t, t, 1.f);
-          float c = rsqrtf(g);
-          c = c * fmaf(-0.5f * g * c, c, 1.5f);
-          const float sv = t * c;
-          const float2 e = cscale(apq, ir);
+          big |= (r2 > PT::kBig2 * den);
+          const T ir = rsq_nr(r2);
+          const T tau = T(0.5) * (aqq - app) * ir;
+          const T h = fmaT(tau, tau, T(1));
+          const T t = copysignT(rcp_fast(absT(tau) + sqrt_h(h)), tau);
+          const T g = fmaT(t, t, T(1));
+          const T c = rsq_nr(g);
+          const T sv = t * c;
+          const C e = cscale(apq, ir);
           if (i == p) {  // J_pp = c, J_qp = -s conj(e)
-            Jii = make_float2(c, 0.f);
+            Jii = mkc<T>(c, T(0));
             Joi = cscale(cconj(e), -sv);
           } else {       // J_qq = c conj(e), J_pq = s
             Jii = cscale(cconj(e), c);
-            Joi = make_float2(sv, 0.f);
+            Joi = mkc<T>(sv, T(0));
           }
         }
       }
       rotated |= act;
       // J of the column index j: computed by lane (j, 0), whose row index is j.
-      const float2 Jll = shfl2(Jii, own ? j * M : lane);
-      const float2 Jol = shfl2(Joi, own ? j * M : lane);
+      const C Jll = shfl2(Jii, own ? j * M : lane);
+      const C Jol = shfl2(Joi, own ? j * M : lane);
       const bool ip_ok = pi < M, jp_ok = pj < M;
-      const float2 W_il2 = shfl2(W, own && jp_ok ? i * M + pj : lane);
-      const float2 W_i2l = shfl2(W, own && ip_ok ? pi * M + j : lane);
-      const float2 W_i2l2 = shfl2(W, own && ip_ok && jp_ok ? pi * M + pj : lane);
-      const float2 V_il2 = shfl2(V, own && jp_ok ? i * M + pj : lane);
+      const C W_il2 = shfl2(W, own && jp_ok ? i * M + pj : lane);
+      const C W_i2l = shfl2(W, own && ip_ok ? pi * M + j : lane);
+      const C W_i2l2 = shfl2(W, own && ip_ok && jp_ok ? pi * M + pj : lane);
+      const C V_il2 = shfl2(V, own && jp_ok ? i * M + pj : lane);
       // W' = J^H W J restricted to entry (i, j); V' = V J.
-      float2 r0 = cmul(W, Jll), r1 = cmul(W_i2l, Jll);
+      C r0 = cmul(W, Jll), r1 = cmul(W_i2l, Jll);
       if (jp_ok) {
         r0 = cfma(W_il2, Jol, r0);
         r1 = cfma(W_i2l2, Jol, r1);
       }
-      float2 Wn = ccmul(Jii, r0);
+      C Wn = ccmul(Jii, r0);
       if (ip_ok) Wn = cadd(Wn, ccmul(Joi, r1));
-      float2 Vn = cmul(V, Jll);
+      C Vn = cmul(V, Jll);
       if (jp_ok) Vn = cfma(V_il2, Jol, Vn);
-      if (i == j) Wn.y = 0.f;
-      if (act && j == pi) Wn = make_float2(0.f, 0.f);  // the pivot pair
+      if (i == j) Wn.y = T(0);
+      if (act && j == pi) Wn = mkc<T>(T(0), T(0));  // the pivot pair
       W = Wn;
       V = Vn;
     }
@@ -767,26 +869,26 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
       sweeps = sweep + 1;
       break;
     }
-    const float di = __shfl_sync(0xffffffffu, W.x, own ? i * M + i : lane);
-    const float dj = __shfl_sync(0xffffffffu, W.x, own ? j * M + j : lane);
-    const float gap = dj - di;
+    const T di = __shfl_sync(0xffffffffu, W.x, own ? i * M + i : lane);
+    const T dj = __shfl_sync(0xffffffffu, W.x, own ? j * M + j : lane);
+    const T gap = dj - di;
     // (Every gap must also stand clear of the eigenvalues' size: degenerate pairs take
     // another sweep.)
     const bool small = !own || i == j ||
-                       (cabs2(W) <= 4e-8f * gap * gap && fabsf(gap) > 1e-5f * fmaxf(fabsf(di), fabsf(dj)));
+                       (cabs2(W) <= PT::kFirst2 * gap * gap && absT(gap) > PT::kGap * maxT(absT(di), absT(dj)));
     if (__all_sync(0xffffffffu, small)) {
       // First-order step: V <- V (I + X), X_ij = W_ij / (d_j - d_i);
       // d_j += sum_p |W_pj|^2 / (d_j - d_p).
-      const float2 X = (own && i != j) ? cscale(W, __fdividef(1.f, gap)) : make_float2(0.f, 0.f);
-      float2 Vn = V;
+      const C X = (own && i != j) ? cscale(W, rcp_fast(gap)) : mkc<T>(T(0), T(0));
+      C Vn = V;
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        const float2 vim = shfl2(V, own ? i * M + m : lane);
-        const float2 xmj = shfl2(X, own ? m * M + j : lane);
+        const C vim = shfl2(V, own ? i * M + m : lane);
+        const C xmj = shfl2(X, own ? m * M + j : lane);
         Vn = cfma(vim, xmj, Vn);
       }
-      const float e2 = W.x * X.x + W.y * X.y;  // |W_ij|^2 / (d_j - d_i)
-      float corr = 0.f;
+      const T e2 = W.x * X.x + W.y * X.y;  // |W_ij|^2 / (d_j - d_i)
+      T corr = T(0);
 #pragma unroll
       for (int m = 0; m < M; ++m) corr += __shfl_sync(0xffffffffu, e2, own ? m * M + j : lane);
       V = Vn;
@@ -797,10 +899,10 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
   }
   if (sweeps < 0) return kErrEigNoConv;
   // 4. Outputs: Sig, Q = Li^H V (Q_ij = sum_{k>=i} conj(Li_ki) V_kj), U = V.
-  float2 Qv = make_float2(0.f, 0.f);
+  C Qv = mkc<T>(T(0), T(0));
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const float2 vkj = shfl2(V, own ? k * M + j : lane);
+    const C vkj = shfl2(V, own ? k * M + j : lane);
     if (k >= i) Qv = cadd(Qv, ccmul(B[k][i], vkj));
   }
   if (own) {
@@ -808,18 +910,211 @@ __device__ int warp_gevd_reg(const float2 (*A)[kMaxM], float2 (*B)[kMaxM], float
     Uout[i][j] = V;
     if (i == j) sig[i] = W.x;
   }
-  const bool pos = !own || i != j || ((W.x > 0.f) && (W.x < 3.0e38f));
+  const bool pos = !own || i != j || ((W.x > T(0)) && (W.x < PT::kHuge));
   *ldL = ld;
   __syncwarp();
   return __all_sync(0xffffffffu, pos) ? kOk : kErrNotPD;
 }
 
-// ||U||_F^2 - M in FP64 (all lanes get the result).
+// ---------------------------------------- Newton-type iteration for the joint diagonaliser
+// One step of the Newton-type correction of a generalised eigenbasis of the Hermitian pencil
+// (A, B), B positive definite: the correction of Ogita and Aishima ("Iterative refinement for
+// symmetric eigenvalue decomposition", 2018) written for the pencil. With R = I - X^H B X and
+// S = X^H A X, lam_i = s_ii / (1 - r_ii), E_ii = r_ii / 2, E_ij = (s_ij + lam_j r_ij) /
+// (lam_j - lam_i) for i != j, and X <- X (I + E). To first order in R and the off-diagonal
+// part of S this makes X^H B X = I and X^H A X = diag(lam), so the residuals square with each
+// step. A pair whose eigenvalues lie closer than kSep of their size cannot be separated this
+// way and takes E_ij = r_ij / 2 (its invariant subspace is still refined). T1, T2: workspace.
+// Writes lam (the Rayleigh quotients of the incoming X) and returns max_ij |E_ij|_1 (all
+// lanes; NaN propagates). With first = true, X is taken to be the identity (not read): R =
+// I - B and S = A. All 32 lanes; ends with __syncwarp().
+template <int M, typename T>
+__device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], Cx<T> (*X)[kMaxM],
+                              Cx<T> (*T1)[kMaxM], Cx<T> (*T2)[kMaxM], T* lam, bool first,
+                              int lane, T* trR = nullptr) {
+  using C = Cx<T>;
+  constexpr int MM = M * M;
+  constexpr int kPer = (MM + 31) / 32;
+  constexpr T kSep = sizeof(T) == 8 ? T(1e-12) : T(1e-6);
+  if (!first) {
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {  // T1 = B X, T2 = A X
+      const int e = lane + 32 * t;
+      if (e < MM) {
+        const int i = e / M, j = e % M;
+        C b = mkc<T>(T(0), T(0)), a = mkc<T>(T(0), T(0));
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          b = cfma(B[i][k], X[k][j], b);
+          a = cfma(A[i][k], X[k][j], a);
+        }
+        T1[i][j] = b;
+        T2[i][j] = a;
+      }
+    }
+    __syncwarp();
+  }
+  C r[kPer], sv[kPer];
+  T tr = T(0);
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {  // R = I - X^H T1, S = X^H T2
+    const int e = lane + 32 * t;
+    r[t] = sv[t] = mkc<T>(T(0), T(0));
+    if (e < MM) {
+      const int i = e / M, j = e % M;
+      C q, u;
+      if (first) {
+        q = B[i][j];
+        u = A[i][j];
+      } else {
+        q = u = mkc<T>(T(0), T(0));
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          q = cfma(cconj(X[k][i]), T1[k][j], q);
+          u = cfma(cconj(X[k][i]), T2[k][j], u);
+        }
+      }
+      r[t] = mkc<T>((i == j ? T(1) : T(0)) - q.x, -q.y);
+      sv[t] = u;
+      if (i == j) {
+        lam[i] = u.x * rcp_fast(T(1) - r[t].x);
+        tr += r[t].x;
+      }
+    }
+  }
+  if (trR) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    *trR = tr;
+  }
+  __syncwarp();
+  T emax = T(0);
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {  // E into T1
+    const int e = lane + 32 * t;
+    if (e < MM) {
+      const int i = e / M, j = e % M;
+      C ev;
+      if (i == j) {
+        ev = mkc<T>(T(0.5) * r[t].x, T(0));
+      } else {
+        const T li = lam[i], lj = lam[j], gap = lj - li;
+        if (absT(gap) > kSep * maxT(absT(li), absT(lj))) {
+          const T rg = rcp_fast(gap);
+          ev = mkc<T>(fmaT(lj, r[t].x, sv[t].x) * rg, fmaT(lj, r[t].y, sv[t].y) * rg);
+        } else {
+          ev = mkc<T>(T(0.5) * r[t].x, T(0.5) * r[t].y);
+        }
+      }
+      T1[i][j] = ev;
+      const T m = absT(ev.x) + absT(ev.y);
+      emax = (m > emax || m != m) ? m : emax;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const T other = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = (other > emax || other != other) ? other : emax;
+  }
+  __syncwarp();
+  C xn[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {  // X <- X + X E (from the identity: I + E)
+    const int e = lane + 32 * t;
+    if (e < MM) {
+      const int i = e / M, j = e % M;
+      if (first) {
+        xn[t] = cadd(T1[i][j], mkc<T>(i == j ? T(1) : T(0), T(0)));
+      } else {
+        C x = X[i][j];
+#pragma unroll
+        for (int k = 0; k < M; ++k) x = cfma(X[i][k], T1[k][j], x);
+        xn[t] = x;
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = lane + 32 * t;
+    if (e < MM) X[e / M][e % M] = xn[t];
+  }
+  __syncwarp();
+  return emax;
+}
+
+// FP64 working arrays of the refined eigensolver (shared memory).
+struct RefineWork {
+  double2 A[kMaxM][kMaxM];   // the pencil (A, B) in FP64, B positive definite
+  double2 B[kMaxM][kMaxM];
+  double2 X[kMaxM][kMaxM];   // the basis being refined
+  double2 T1[kMaxM][kMaxM];  // workspace
+  double2 T2[kMaxM][kMaxM];
+  float2 X0[kMaxM][kMaxM];   // the FP32 start (fallback solver's basis)
+  float sig0[kMaxM];
+  float lam32[kMaxM];
+  double lam[kMaxM];
+};
+
+// FP64 refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B): Newton-type steps
+// (warp_newton_step) in FP64, one, or two when the first correction exceeded 1e-4 (a poor
+// start); the result is X^H B X = I and X^H A X = diag(lam) to second order in the FP32
+// residuals. Leaves X in w.X and lam in w.lam. All 32 lanes; ends with __syncwarp().
 template <int M>
-__device__ double unitarity_defect(const float2 (*U)[kMaxM], int lane) {
+__device__ void warp_refine_gevd(RefineWork& w, const float2 (*X0)[kMaxM], int lane) {
+  for (int e = lane; e < M * M; e += 32) w.X[e / M][e % M] = c2z(X0[e / M][e % M]);
+  __syncwarp();
+  for (int step = 0; step < 2; ++step) {
+    const double em = warp_newton_step<M, double>(w.A, w.B, w.X, w.T1, w.T2, w.lam, false, lane);
+    if (!(em > 1e-4)) break;  // converged to second order (also leaves on NaN)
+  }
+}
+
+// log det B of a Hermitian positive definite B near the identity (FP64, shared memory), by an
+// FP32 Cholesky factorisation on one lane written in terms of H = B - I (formed in FP64):
+// the pivots are 1 + delta_k with delta_k = H_kk - sum_{m<k} |L_km|^2 computed from small
+// quantities, and log det B = sum_k log1p(delta_k). Rounding then perturbs the result by about
+// 2^-24 |H| rather than 2^-24 (the Grams of a converging FastFCA iteration are close to the
+// identity in the current basis). Returns the value on every lane; NaN if a pivot is not
+// positive.
+template <int M>
+__device__ double warp_logdet_hpd32(const double2 (*B)[kMaxM], int lane) {
+  double ld = 0.0;
+  if (lane == 0) {
+    float2 L[M][M];
+    float il[M];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+      for (int i = j; i < M; ++i) {
+        const double2 bij = B[i][j];
+        float2 s = make_float2((float)(i == j ? bij.x - 1.0 : bij.x), (float)bij.y);
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = csub(s, cmulc(L[i][k], L[j][k]));
+        if (i == j) {
+          const float d = s.x;  // pivot - 1
+          ok = ok && (d > -1.f) && (d < 3.0e38f);
+          ld += (double)log1pf(d);
+          const float p = 1.f + d;
+          il[j] = rsq_nr(p);
+          L[j][j] = make_float2(p * il[j], 0.f);
+        } else {
+          L[i][j] = cscale(s, il[j]);
+        }
+      }
+    }
+    if (!ok) ld = __longlong_as_double(0x7ff8000000000000ll);
+  }
+  return __shfl_sync(0xffffffffu, ld, 0);
+}
+
+// ||U||_F^2 - M in FP64 (all lanes get the result).
+template <int M, typename C>
+__device__ double unitarity_defect(const C (*U)[kMaxM], int lane) {
   double un = 0.0;
   for (int e = lane; e < M * M; e += 32) {
-    const float2 u = U[e / M][e % M];
+    const C u = U[e / M][e % M];
     un = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, un));
   }
 #pragma unroll
@@ -827,9 +1122,9 @@ __device__ double unitarity_defect(const float2 (*U)[kMaxM], int lane) {
   return un - (double)M;
 }
 
-// P <- P Q in FP64 (Eq. (updatePeff)) with Q given explicitly (FP32).
-template <int M>
-__device__ void warp_update_basis_q(double2 (*P)[kMaxM], const float2 (*Q)[kMaxM], int lane) {
+// P <- P Q in FP64 (Eq. (updatePeff)) with Q given explicitly (FP32 or FP64).
+template <int M, typename C>
+__device__ void warp_update_basis_q(double2 (*P)[kMaxM], const C (*Q)[kMaxM], int lane) {
   constexpr int kPer = (M * M + 31) / 32;
   double2 out[kPer];
 #pragma unroll
@@ -852,11 +1147,12 @@ __device__ void warp_update_basis_q(double2 (*P)[kMaxM], const float2 (*Q)[kMaxM
   __syncwarp();
 }
 
-// P <- P Q in FP64 (Eq. (updatePeff)) with Q given explicitly (FP32), for 2 M^2 <= 32: lane
-// 2e + part computes the real (part 0) or imaginary (part 1) part of entry e as a pairwise sum
-// of its 2M products, which keeps the chain of dependent FP64 operations short.
-template <int M>
-__device__ void warp_update_basis_q2(double2 (*P)[kMaxM], const float2 (*Q)[kMaxM], int lane) {
+// P <- P Q in FP64 (Eq. (updatePeff)) with Q given explicitly (FP32 or FP64), for
+// 2 M^2 <= 32: lane 2e + part computes the real (part 0) or imaginary (part 1) part of entry
+// e as a pairwise sum of its 2M products, which keeps the chain of dependent FP64 operations
+// short.
+template <int M, typename C>
+__device__ void warp_update_basis_q2(double2 (*P)[kMaxM], const C (*Q)[kMaxM], int lane) {
   static_assert(2 * M * M <= 32, "one real part per lane");
   const int e = lane >> 1, part = lane & 1;
   const int i = e / M, c = e % M;
@@ -879,34 +1175,6 @@ __device__ void warp_update_basis_q2(double2 (*P)[kMaxM], const float2 (*Q)[kMax
   if (e < M * M) {
     if (part) P[i][c].y = v;
     else P[i][c].x = v;
-  }
-  __syncwarp();
-}
-
-// P <- P Q in FP64 (Eq. (updatePeff)); P in shared memory [M][M] double2, Q = la.V (FP32).
-template <int M>
-__device__ void warp_update_basis(double2 (*P)[kMaxM], const WarpLA& la, int lane) {
-  constexpr int kPer = (M * M + 31) / 32;
-  double2 out[kPer];
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int e = lane + 32 * t;
-    if (e < M * M) {
-      const int i = e / M, c = e - (e / M) * M;
-      double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int m = 0; m < M; ++m) s = zfma(P[i][m], c2z(la.V[m][c]), s);
-      out[t] = s;
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int e = lane + 32 * t;
-    if (e < M * M) {
-      const int i = e / M, c = e - (e / M) * M;
-      P[i][c] = out[t];
-    }
   }
   __syncwarp();
 }

@@ -1,5 +1,6 @@
 // Launchers of the FastFCA kernels (fca_fast.cuh): the fused EM kernel with 128 threads per
-// CTA for both storages, and the posterior-mean kernel.
+// CTA for both storages (FP32 eigensolver; the FP64 and refined ones are in fca_fast64.cu and
+// fca_fast_refined.cu), and the posterior-mean kernel.
 #include "fca_fast.cuh"
 
 namespace fca {
@@ -17,10 +18,13 @@ bool fast_threads_batch(int storage, int threads) {
 
 cudaError_t launch_fast_em(int M, int storage, const FastEmArgs& a, cudaStream_t st, int threads) {
   if (a.bins) {
-    if (!fast_threads_batch(storage, threads)) return cudaErrorInvalidValue;
+    if (!fast_threads_batch(storage, threads) || a.gevd_mode) return cudaErrorInvalidValue;
     return launch_fast_batch_c64(M, a, st, threads);
   }
   if (threads != 128) return cudaErrorInvalidValue;
+  if (a.gevd_mode == 1) return launch_fast_single_g64(M, storage, a, st);
+  if (a.gevd_mode == 2) return launch_fast_single_refined(M, storage, a, st);
+  if (a.gevd_mode != 0) return cudaErrorInvalidValue;
   return storage ? launch_fast_nt<1, 128, false>(M, a, st) : launch_fast_nt<0, 128, false>(M, a, st);
 }
 

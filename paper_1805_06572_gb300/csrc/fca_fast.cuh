@@ -12,9 +12,11 @@
 //     St_j += (mut_j mut_j^H + diag(c)) / v_j'          Eq. (updateStildeeff), partial sums
 //     log-likelihood terms log d_i + |yt_i|^2 / d_i     Eq. (like) in the transformed basis
 //   CTA reduction: per-lane FP32 partials -> warp transpose-reduction (FP32) -> cross-warp
-//     merge in FP64, in a fixed order (bitwise reproducible);
-//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8) and the next
-//     basis P^H for the bin pass; meanwhile warp 1 does the previous iteration's FP64
+//     merge in a fixed order (bitwise reproducible): the Gram entries in the precision G of
+//     the eigensolver they feed (FP32, or FP64), the log-likelihood sums compensated into
+//     FP64;
+//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8) in precision G and
+//     the next basis P^H for the bin pass; meanwhile warp 1 does the previous iteration's FP64
 //     bookkeeping: P <- P Q (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)),
 //     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use), and the
 //     previous iteration's log-likelihood.
@@ -22,13 +24,28 @@
 // y^H Rx^-1 y = sum_i |yt_i|^2 / d_i, which follow from Rx = P^-H (v1 Lam + v2 I) P^-1.
 // The mixture and v stay in shared memory across iterations when they fit.
 #pragma once
+#include <type_traits>
+
 #include "fca_dev.cuh"
 #include "fca_internal.h"
 
 namespace fca {
 
-template <int M, int NW>
+// Precision modes of the per-bin generalised eigenproblem (FCA_GEVD_* in fca.h):
+//   0  FP32 merge of the Gram partials, FP32 Cholesky + Jacobi, FP32 Q;
+//   1  FP64 merge, FP64 Cholesky + Jacobi, FP64 Q;
+//   2  FP64 merge, FP32 Cholesky + Jacobi, then FP64 refinement of Q (warp_refine_gevd).
+template <int GM> struct GevdTypes;
+template <> struct GevdTypes<0> { using Merge = float; using Solve = float; using Out = float; };
+template <> struct GevdTypes<1> { using Merge = double; using Solve = double; using Out = double; };
+template <> struct GevdTypes<2> { using Merge = double; using Solve = float; using Out = double; };
+struct NoRefine {};
+
+template <int M, int NW, int GM>
 struct FastShared {
+  using Ty = GevdTypes<GM>;
+  using SolveT = typename Ty::Solve;
+  using OutT = typename Ty::Out;
   static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
   float red[NW][V];
   double2 P[kMaxM][kMaxM];      // basis P (FP64)
@@ -38,16 +55,30 @@ struct FastShared {
   double lam64[kMaxM];
   // Double-buffered results of an iteration's eigensolve, consumed by the deferred FP64
   // bookkeeping one iteration later.
-  float2 Q[2][kMaxM][kMaxM];
-  float2 U[2][kMaxM][kMaxM];
-  float sig[2][kMaxM];
-  float ldL[2];                 // 2 sum log(1/L_ii): log|det Q|^2 = ldL + log|det U|^2
-  double llt[2][2];             // sum log d, sum p/d of the iteration
+  Cx<OutT> Q[2][kMaxM][kMaxM];
+  Cx<SolveT> U[2][kMaxM][kMaxM];
+  OutT sig[2][kMaxM];
+  OutT ldL[2];       // modes 0, 1: 2 sum log(1/L_ii), log|det Q|^2 = ldL + log|det U|^2;
+                     // mode 2: log|det Q|^2 itself (= -log det St2)
+  double llt[2][2];  // sum log d, sum p/d of the iteration
   double logdetS2;
   int fail;          // read by every thread after a barrier; written only before one
   int fail_pending;  // set by the deferred log-likelihood, read after the iteration's barrier
-  WarpLA la;
+  int wid0;          // hardware warp slot of warp 0 (chooses the warps' roles)
+  WarpLAT<SolveT> la;
+  typename std::conditional<GM == 2, RefineWork, NoRefine>::type rf;
 };
+
+// Warp roles of iteration `it`: the eigensolver (and the publication of the next basis), the
+// deferred basis update and the deferred log-likelihood. A warp issues from the SM
+// sub-partition (scheduler) of its hardware warp slot modulo 4, and the per-bin tail is a
+// long single-warp chain, so the solver's slot rotates with the iteration and with the CTA's
+// first slot: the tails of the CTAs sharing an SM spread over its schedulers instead of all
+// landing on the scheduler of warp 0. (The arithmetic does not depend on the warp.)
+template <int NW>
+__device__ __forceinline__ int solver_warp(int it, int wid0) {
+  return ((it + (wid0 >> 2) - wid0) & 3) % NW;
+}
 
 __host__ __device__ constexpr int pair_index(int M, int i, int k) {  // i < k
   return i * (M - 1) - i * (i - 1) / 2 + (k - i - 1);
@@ -84,6 +115,22 @@ __device__ __forceinline__ void value_entry(int v, int* g, int* i, int* k, int* 
   *k = row + 1 + pr;
 }
 
+// Store one merged Gram value v of entry (i, k) (part: real 0 / imaginary 1) into the
+// Hermitian matrix D (both triangles).
+template <int M, typename C, typename T>
+__device__ __forceinline__ void merge_store(C (*D)[kMaxM], int i, int k, int part, T v) {
+  if (i == k) {
+    D[i][i].x = v;
+    D[i][i].y = T(0);
+  } else if (part == 0) {
+    D[i][k].x = v;
+    D[k][i].x = v;
+  } else {
+    D[i][k].y = v;
+    D[k][i].y = -v;
+  }
+}
+
 // Deferred FP64 bookkeeping of iteration `it`, in two parts that run on two warps at once.
 // Basis part: P <- P Q (Eq. (updatePeff)) and its FP32 copy, Lambda <- Sigma
 // (Eq. (updateLambdaeff)), and at it = L-2 the basis of iteration L-1.
@@ -108,7 +155,7 @@ __device__ void fast_deferred_basis(Sh& sh, const FastEmArgs& a, int f, int it, 
 // Log-likelihood part: the log-likelihood of iteration it (at its own parameters), then
 // log det S2 = -log|det P|^2 of the next basis (subtract log|det Q|^2 of the Q applied), and
 // at it = L-2 that of iteration L-1.
-template <int M, typename Sh>
+template <int M, int GM, typename Sh>
 __device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int it, int lane) {
   const int b = it & 1;
   if (lane == 0) {
@@ -120,7 +167,7 @@ __device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int 
       sh.fail_pending = kErrNonFinite;
     }
   }
-  const double ldQ = (double)sh.ldL[b] + unitarity_defect<M>(sh.U[b], lane);
+  const double ldQ = (GM == 2) ? (double)sh.ldL[b] : (double)sh.ldL[b] + unitarity_defect<M>(sh.U[b], lane);
   if (lane == 0) {
     sh.logdetS2 -= ldQ;
     if (it == a.iters - 2) a.logdetS2_prev[f] = sh.logdetS2;
@@ -130,12 +177,19 @@ __device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int 
 
 // kB: the CTA's bin comes from the descriptor table a.bins (a batch); otherwise bin
 // f = blockIdx.x of one mixture with the [F][N][M] / [2][F][N] layouts and v_in == v.
-template <int M, int ST, int NT, bool kB>
+// GM: precision mode of the per-bin eigensolver and of the cross-warp Gram merge (GevdTypes);
+// the bin pass is FP32 and the basis, log-likelihood and log-determinant bookkeeping FP64 in
+// every mode.
+template <int M, int ST, int NT, bool kB, int GM = 0>
 __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(const FastEmArgs a) {
   using E = typename Elem<ST>::T;
   constexpr int NW = NT / 32;
   static_assert(NW >= 2, "the deferred bookkeeping runs on warp 1");
-  using Sh = FastShared<M, NW>;
+  static_assert(GM != 2 || NW >= 3, "the refined mode computes log det St2 on a third warp");
+  using Sh = FastShared<M, NW, GM>;
+  using MT = typename Sh::Ty::Merge;
+  using ST2 = typename Sh::SolveT;
+  constexpr bool kG64 = GM != 0;  // FP64 basis publication
   constexpr int V = Sh::V;
   constexpr int MM = M * M;
   constexpr bool kHoist = (M <= 4);
@@ -196,6 +250,9 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
     sh.logdetS2 = a.logdetS2[f];
     sh.fail = 0;
     sh.fail_pending = 0;
+    unsigned wslot;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(wslot));
+    sh.wid0 = (int)wslot;
   }
   if (res) {
     const size_t bytes = (size_t)N * M * sizeof(E);
@@ -366,31 +423,23 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
       warp_reduce_store<V>(acc, lane, sh.red[warp]);
     }
     __syncthreads();
-    // Merge the warp partials in a fixed order: Gram entries in FP32 (they feed the FP32
-    // eigensolver), the two log-likelihood sums with a compensated two-float sum kept in
-    // FP64. One value per thread.
+    // Merge the warp partials in a fixed order (pairwise): Gram entries in the eigensolver's
+    // precision G (FP32 sums, or the FP32 warp partials summed in FP64), the two
+    // log-likelihood sums with a compensated two-float sum kept in FP64. One value per thread.
     for (int e = tid; e < V; e += NT) {
       if (e < 2 * MM) {
-        float sv[NW];
+        MT sv[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) sv[w] = sh.red[w][e];
+        for (int w = 0; w < NW; ++w) sv[w] = (MT)sh.red[w][e];
 #pragma unroll
         for (int h = NW / 2; h >= 1; h >>= 1)
 #pragma unroll
           for (int w = 0; w < h; ++w) sv[w] += sv[w + h];
-        const float val = sv[0] * (float)invN;
+        const MT val = sv[0] * (MT)invN;
         int g, i, k, part;
         value_entry<M>(e, &g, &i, &k, &part);
-        float2(*D)[kMaxM] = g ? sh.la.L : sh.la.A;
-        if (i == k) {
-          D[i][i] = make_float2(val, 0.f);
-        } else if (part == 0) {
-          D[i][k].x = val;
-          D[k][i].x = val;
-        } else {
-          D[i][k].y = val;
-          D[k][i].y = -val;
-        }
+        merge_store<M>(g ? sh.la.L : sh.la.A, i, k, part, (ST2)val);
+        if constexpr (GM == 2) merge_store<M>(g ? sh.rf.B : sh.rf.A, i, k, part, (double)val);
       } else {
         float hi = sh.red[0][e], lo = 0.f;
 #pragma unroll
@@ -406,39 +455,95 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
     }
     __syncthreads();
 
-    if (warp == 0) {
-      float ldL = 0.f;
+    const int ws = solver_warp<NW>(it, sh.wid0);  // eigensolver; then basis, log-likelihood
+    const int wb = (ws + 1) % NW, wl = (ws + 2) % NW;
+    if (warp == ws) {
+      ST2 ldL = ST2(0);
       int rc;
-      if constexpr (M <= 4) {
-        rc = warp_gevd_reg<M>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL, 2.0e-7f, 30, lane);
+      if constexpr (GM == 2) {
+        // Newton-type iteration from the identity (the basis P already diagonalises the
+        // previous iteration's parameters, so the new Grams are nearly diagonal in it): FP32
+        // steps, then the FP64 refinement against the FP64 Grams. A poor start (a first
+        // correction above 0.1, or steps that do not converge quadratically) takes the FP32
+        // Cholesky + Jacobi solver instead, whose basis the FP64 steps then refine.
+        rc = kOk;
+        float em = warp_newton_step<M, float>(sh.la.A, sh.la.L, sh.la.V, sh.la.Z, sh.la.A2,
+                                              sh.rf.lam32, true, lane);
+        bool newton = em <= 0.1f;
+        for (int k = 0; newton && em > 1e-5f && k < 4; ++k) {
+          const float en = warp_newton_step<M, float>(sh.la.A, sh.la.L, sh.la.V, sh.la.Z, sh.la.A2,
+                                                      sh.rf.lam32, false, lane);
+          newton = en <= 0.5f * em;
+          em = en;
+        }
+        if (newton) {
+          warp_refine_gevd<M>(sh.rf, sh.la.V, lane);
+        } else {
+          if constexpr (M <= 4) {
+            rc = warp_gevd_reg<M, float>(sh.la.A, sh.la.L, sh.rf.sig0, sh.rf.X0, sh.U[b], &ldL,
+                                         Prec<float>::kTol, a.max_sweeps, lane);
+          } else {
+            rc = warp_gevd_fast<M, float>(sh.la, lane, sh.rf.sig0, sh.rf.X0, sh.U[b], &ldL, a.max_sweeps);
+          }
+          if (rc == kOk) warp_refine_gevd<M>(sh.rf, sh.rf.X0, lane);
+        }
+        if (rc == kOk) {
+          for (int e = lane; e < MM; e += 32) sh.Q[b][e / M][e % M] = sh.rf.X[e / M][e % M];
+          if (lane < M) {
+            const double l = sh.rf.lam[lane];
+            sh.sig[b][lane] = l;
+            if (!(l > 0.0) || !(l < 1e300)) rc = kErrNotPD;
+          }
+          rc = __reduce_max_sync(0xffffffffu, rc);  // warp-uniform
+        }
       } else {
-        rc = warp_gevd_fast<M>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL);
+        if constexpr (M <= 4) {
+          rc = warp_gevd_reg<M, ST2>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL,
+                                     Prec<ST2>::kTol, a.max_sweeps, lane);
+        } else {
+          rc = warp_gevd_fast<M, ST2>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL, a.max_sweeps);
+        }
+        if (lane == 0) sh.ldL[b] = ldL;
       }
-      if (lane == 0) sh.ldL[b] = ldL;
       if (rc != kOk && lane == 0) {
         set_status(a.status, rc);
         sh.fail = rc;
       }
-    } else if (warp == 1 && it > 0) {
+    } else if (warp == wb && it > 0) {
       fast_deferred_basis<M>(sh, a, f, it - 1, lane);
-      if constexpr (NW < 3) fast_deferred_ll<M>(sh, a, f, N, it - 1, lane);
-    } else if (NW >= 3 && warp == 2 && it > 0) {
-      fast_deferred_ll<M>(sh, a, f, N, it - 1, lane);
+      if constexpr (NW < 3) fast_deferred_ll<M, GM>(sh, a, f, N, it - 1, lane);
+    } else if (NW >= 3 && warp == wl) {
+      // Refined mode: the basis Q of this iteration is St2-orthonormal, so
+      // log|det Q|^2 = -log det St2.
+      if constexpr (GM == 2) {
+        const double ld = warp_logdet_hpd32<M>(sh.rf.B, lane);
+        if (lane == 0) sh.ldL[b] = -ld;
+      }
+      if (it > 0) fast_deferred_ll<M, GM>(sh, a, f, N, it - 1, lane);
     }
-    if (warp < 2) asm volatile("bar.sync 1, 64;" ::: "memory");
-    if (warp == 0) {
+    if (warp == ws || warp == wb) asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (warp == ws) {
       if (!sh.fail) {
-        // Publish the next basis for the bin pass: P^H <- (P Q)^H from the FP32 copies.
+        // Publish the next basis for the bin pass: P^H <- (P Q)^H, from the FP32 copies (FP32
+        // eigensolver) or in FP64 and then rounded (FP64 eigensolver).
         for (int e = lane; e < MM; e += 32) {
           const int i = e / M, m = e % M;  // (P Q)_{m i}
-          float2 s = make_float2(0.f, 0.f);
+          if constexpr (kG64) {
+            double2 s = make_double2(0.0, 0.0);
 #pragma unroll
-          for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
-          sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
+            for (int k = 0; k < M; ++k) s = zfma(sh.P[m][k], sh.Q[b][k][i], s);
+            sh.PH[i][m] = make_float2((float)s.x * gi, -(float)s.y * gi);
+          } else {
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
+            sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
+          }
         }
         if (lane < M) {
-          sh.lam[lane] = sh.sig[b][lane];
-          sh.ilam[lane] = 1.f / sh.sig[b][lane];
+          const float sg = (float)sh.sig[b][lane];
+          sh.lam[lane] = sg;
+          sh.ilam[lane] = 1.f / sg;
         }
       }
     }
@@ -449,9 +554,9 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
   if (done > 0 && done == a.iters) {
     if (warp == 1) {
       fast_deferred_basis<M>(sh, a, f, done - 1, lane);
-      if constexpr (NW < 3) fast_deferred_ll<M>(sh, a, f, N, done - 1, lane);
+      if constexpr (NW < 3) fast_deferred_ll<M, GM>(sh, a, f, N, done - 1, lane);
     } else if (NW >= 3 && warp == 2) {
-      fast_deferred_ll<M>(sh, a, f, N, done - 1, lane);
+      fast_deferred_ll<M, GM>(sh, a, f, N, done - 1, lane);
     }
   }
   __syncthreads();
@@ -554,10 +659,10 @@ __global__ void __launch_bounds__(256) sep_fast_kernel(const SepFastArgs a) {
 
 
 // Host-side launch of fast_em_kernel<M, ST, NT> (instantiated per translation unit).
-template <int M, int ST, int NT, bool kB>
+template <int M, int ST, int NT, bool kB, int GM = 0>
 cudaError_t launch_fast_t(const FastEmArgs& a, cudaStream_t st) {
   const size_t dyn = (size_t)a.res_bytes;
-  auto k = fast_em_kernel<M, ST, NT, kB>;
+  auto k = fast_em_kernel<M, ST, NT, kB, GM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
@@ -571,17 +676,17 @@ cudaError_t launch_fast_t(const FastEmArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int ST, int NT, bool kB>
+template <int ST, int NT, bool kB, int GM = 0>
 cudaError_t launch_fast_nt(int M, const FastEmArgs& a, cudaStream_t st) {
   switch (M) {
-    case 1: return launch_fast_t<1, ST, NT, kB>(a, st);
-    case 2: return launch_fast_t<2, ST, NT, kB>(a, st);
-    case 3: return launch_fast_t<3, ST, NT, kB>(a, st);
-    case 4: return launch_fast_t<4, ST, NT, kB>(a, st);
-    case 5: return launch_fast_t<5, ST, NT, kB>(a, st);
-    case 6: return launch_fast_t<6, ST, NT, kB>(a, st);
-    case 7: return launch_fast_t<7, ST, NT, kB>(a, st);
-    case 8: return launch_fast_t<8, ST, NT, kB>(a, st);
+    case 1: return launch_fast_t<1, ST, NT, kB, GM>(a, st);
+    case 2: return launch_fast_t<2, ST, NT, kB, GM>(a, st);
+    case 3: return launch_fast_t<3, ST, NT, kB, GM>(a, st);
+    case 4: return launch_fast_t<4, ST, NT, kB, GM>(a, st);
+    case 5: return launch_fast_t<5, ST, NT, kB, GM>(a, st);
+    case 6: return launch_fast_t<6, ST, NT, kB, GM>(a, st);
+    case 7: return launch_fast_t<7, ST, NT, kB, GM>(a, st);
+    case 8: return launch_fast_t<8, ST, NT, kB, GM>(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -589,5 +694,9 @@ cudaError_t launch_fast_nt(int M, const FastEmArgs& a, cudaStream_t st) {
 // Defined in fca_fast_tuned.cu: batches (descriptor tables), complex64 storage, 64, 128 or
 // 256 threads per CTA.
 cudaError_t launch_fast_batch_c64(int M, const FastEmArgs& a, cudaStream_t st, int threads);
+// Defined in fca_fast64.cu (mode 1) and fca_fast_refined.cu (mode 2): one mixture, 128 threads
+// per CTA.
+cudaError_t launch_fast_single_g64(int M, int storage, const FastEmArgs& a, cudaStream_t st);
+cudaError_t launch_fast_single_refined(int M, int storage, const FastEmArgs& a, cudaStream_t st);
 
 }  // namespace fca

@@ -5,6 +5,11 @@
 
 namespace fca {
 
+// Default sweep cap of the Jacobi eigensolver (FCA_ERR_EIG_NOCONV past it) and default
+// precision mode of FastFCA's per-bin eigensolver and Gram merge (FCA_GEVD_* of fca.h).
+constexpr int kDefaultSweeps = 30;
+constexpr int kDefaultGevdMode = 0;
+
 // One frequency bin of a batch of mixtures: where its time-frequency points and source
 // powers live, and which entry of the per-bin parameter arrays it owns. A kernel given a
 // descriptor table handles bins[blockIdx] instead of bin f = blockIdx of one mixture whose
@@ -45,6 +50,8 @@ struct FastEmArgs {
   double* logdetS2_prev;
   double* llf;              // [iters][F] out: per-bin log-likelihood of every iteration
   int* status;
+  int max_sweeps;           // Jacobi sweep cap of the per-bin eigensolver
+  int gevd_mode;            // eigensolver precision mode (FCA_GEVD_*; modes 1, 2 one mixture only)
 };
 
 // Arguments of the fused conventional EM kernel (one CTA per frequency bin).
@@ -105,6 +112,8 @@ struct ParamArgs {
   float2* PinvH;            // [F][M][M]
   float* lam32;             // [F][M]
   int* status;
+  int max_sweeps;           // gevd_from_S: Jacobi sweep cap
+  int gevd_mode;            // gevd_from_S: 0 = FP32 eigensolver, else FP64
 };
 
 // Fused EM kernels. FastFCA: threads per CTA 128 for one mixture; 64, 128 or 256 for a
@@ -135,6 +144,8 @@ struct PrepareExtra {
   double2* P;
   double* lam;
   double* logdetS2;
+  int max_sweeps;           // Jacobi sweep cap of the eigensolver
+  int gevd_mode;            // 0: FP32 eigensolver, else FP64
 };
 cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
                            const double* v0, float* v, float* vfloor, int* status,

@@ -76,6 +76,8 @@ Layout layout(int M, int F, int N, int iters) {
   return L;
 }
 
+bool aligned(const void* ptr, size_t a) { return reinterpret_cast<uintptr_t>(ptr) % a == 0; }
+
 bool on_device(const void* ptr, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
@@ -102,6 +104,11 @@ extern "C" fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const
   for (const void* q : ptrs)
     if (!on_device(q, dev)) return FCA_ERR_ARG;
   if (loglik_dev && !on_device(loglik_dev, dev)) return FCA_ERR_ARG;
+  // The kernels read the caller's buffers in place with vector loads (no staging copy as in
+  // fca_init): y and S0 by 16 bytes, v0 and the outputs by their element size.
+  if (!aligned(y_dev, 16) || !aligned(S0_dev, 16) || !aligned(v0_dev, 8) || !aligned(v_dev, 4) ||
+      !aligned(x1_dev, 8) || !aligned(x2_dev, 8) || (loglik_dev && !aligned(loglik_dev, 8)))
+    return FCA_ERR_ARG;
   unsigned char* base = nullptr;
   if (scratch_for_device(dev, &base) != cudaSuccess) return FCA_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
@@ -128,6 +135,8 @@ extern "C" fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const
   NA_CHECK(cudaMemsetAsync(status, 0, sizeof(int), st));
   // One pass: the floor and initial v, and the generalised eigenproblem of S0 (Eq. (GEVD)).
   fca::PrepareExtra ex = {};
+  ex.max_sweeps = fca::kDefaultSweeps;
+  ex.gevd_mode = fca::kDefaultGevdMode;
   ex.S = reinterpret_cast<const double2*>(S0_dev);
   ex.P = P;
   ex.lam = lam;
@@ -156,6 +165,8 @@ extern "C" fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const
     a.logdetS2_prev = ldet_prev;
     a.llf = llf;
     a.status = status;
+    a.max_sweeps = fca::kDefaultSweeps;
+    a.gevd_mode = fca::kDefaultGevdMode;
     NA_CHECK(fca::launch_fast_em(M, FCA_STORE_C64, a, st));
     fca::note_launches(1);
     if (loglik_dev) {
@@ -188,9 +199,11 @@ extern "C" fca_status fca_em_fast_noalloc(int32_t M, int32_t F, int32_t N, const
   s.x2 = static_cast<float2*>(x2_dev);
   NA_CHECK(fca::launch_sep_fast(M, FCA_STORE_C64, s, st));
   fca::note_launches(1);
-  NA_CHECK(cudaStreamSynchronize(st));
+  // Read the status word on the call's own stream (a plain cudaMemcpy would also wait for
+  // every other blocking stream of the device).
   int code = 0;
-  NA_CHECK(cudaMemcpy(&code, status, sizeof(int), cudaMemcpyDeviceToHost));
+  NA_CHECK(cudaMemcpyAsync(&code, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NA_CHECK(cudaStreamSynchronize(st));
 #undef NA_CHECK
   return (fca_status)code;
 }

@@ -216,6 +216,8 @@ cudaError_t launch_request(fca_server* s, const fca_request& r, unsigned char* b
   // FastFCA requests solve the generalised eigenproblem of S0 (Eq. (GEVD)) in the same pass.
   PrepareExtra ex;
   std::memset(&ex, 0, sizeof(ex));
+  ex.max_sweeps = kDefaultSweeps;
+  ex.gevd_mode = kDefaultGevdMode;
   if (r.form == FCA_FORM_FAST) {
     ex.S = S0;
     ex.P = reinterpret_cast<double2*>(blk + L.P);
@@ -249,6 +251,8 @@ cudaError_t launch_request(fca_server* s, const fca_request& r, unsigned char* b
       a.logdetS2_prev = reinterpret_cast<double*>(blk + L.ldet_prev);
       a.llf = llf;
       a.status = status;
+      a.max_sweeps = kDefaultSweeps;
+      a.gevd_mode = kDefaultGevdMode;
       S_TRY(launch_fast_em(M, 0, a, st));
       ++nk;
     }

@@ -20,6 +20,8 @@ FCA_STORE_C64, FCA_STORE_F16_SCALED = 0, 1
 FCA_MEM_DEVICE, FCA_MEM_HOST = 0, 1
 FCA_SEP_ALG1, FCA_SEP_FINAL_PARAMS = 0, 1
 FCA_FORM_FAST, FCA_FORM_CONVENTIONAL = 0, 1
+FCA_GEVD_FP32, FCA_GEVD_FP64, FCA_GEVD_REFINED = 0, 1, 2
+FCA_MAX_SWEEPS_LIMIT = 1000
 STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NOMEM",
                 4: "FCA_ERR_NOT_PD", 5: "FCA_ERR_EIG_NOCONV", 6: "FCA_ERR_NONFINITE",
                 7: "FCA_ERR_TIMEOUT", 8: "FCA_ERR_STATE", 9: "FCA_ERR_SCRATCH"}
@@ -28,7 +30,7 @@ FCA_NOALLOC_SCRATCH_BYTES = 8 << 20
 # Every entry point declared in include/fca.h.
 EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em_fast_recover",
            "fca_separate", "fca_get_params", "fca_loglik_bins", "fca_last_em_kernel_ms",
-           "fca_kernel_launches",
+           "fca_kernel_launches", "fca_set_eigensolver", "fca_measure_peaks",
            "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
            "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
            "fca_batch_tune", "fca_batch_shape", "fca_batch_set_shape", "fca_batch_sync_status",
@@ -98,6 +100,10 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_last_em_kernel_ms.argtypes = [V, ctypes.POINTER(ctypes.c_float)]
     lib.fca_kernel_launches.argtypes = []
     lib.fca_kernel_launches.restype = ctypes.c_uint64
+    lib.fca_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.fca_measure_peaks.restype = ctypes.c_int
+    lib.fca_set_eigensolver.argtypes = [V, I, I]
+    lib.fca_set_eigensolver.restype = ctypes.c_int
     lib.fca_sync_status.argtypes = [V, V]
     lib.fca_free.argtypes = [V]
     lib.fca_free.restype = None
@@ -268,6 +274,20 @@ def fca_kernel_launches() -> int:
     return int(lib.fca_kernel_launches())
 
 
+def fca_set_eigensolver(state: State, precision: int = FCA_GEVD_FP32, max_sweeps: int = 30):
+    """Precision of FastFCA's per-bin eigensolver and Gram merge (FCA_GEVD_FP32, _FP64 or
+    _REFINED) and its Jacobi sweep cap."""
+    _check(lib.fca_set_eigensolver(ctypes.c_void_p(state.handle), int(precision), int(max_sweeps)),
+           "fca_set_eigensolver")
+
+
+def fca_measure_peaks():
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.fca_measure_peaks(ctypes.byref(a), ctypes.byref(b)), "fca_measure_peaks")
+    return a.value, b.value
+
+
 def fca_sync_status(state: State, stream=None) -> int:
     return int(lib.fca_sync_status(ctypes.c_void_p(state.handle), ctypes.c_void_p(_stream(stream))))
 
@@ -278,10 +298,31 @@ def fca_free(state: State):
         state.handle = None
 
 
+def _expect(t, name, dtype, shape, dev):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be {dtype} {list(shape)}, got {t.dtype} {list(t.shape)}")
+    if not t.is_contiguous() or t.device != dev:
+        raise ValueError(f"{name} must be contiguous and on {dev}")
+
+
 def fca_em_fast_noalloc(y, v0, S0, iters: int, v, x1, x2, loglik=None, stream=None) -> int:
     """FastFCA on caller-owned device tensors with the library's fixed scratch array (no
-    device allocation). Synchronises the stream; returns the status code."""
+    device allocation). Synchronises the stream; returns the status code. Shapes, dtypes,
+    contiguity and device are checked here (the library can only check pointers)."""
+    if y.dim() != 3:
+        raise ValueError("y must be complex64 [F,N,M]")
     F, N, M = y.shape
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _expect(y, "y", torch.complex64, (F, N, M), dev)
+    _expect(v0, "v0", torch.float64, (2, F, N), dev)
+    _expect(S0, "S0", torch.complex128, (2, F, M, M), dev)
+    _expect(v, "v", torch.float32, (2, F, N), dev)
+    _expect(x1, "x1", torch.complex64, (F, N, M), dev)
+    _expect(x2, "x2", torch.complex64, (F, N, M), dev)
+    if loglik is not None:
+        if loglik.dtype != torch.float64 or loglik.numel() < iters or not loglik.is_contiguous() \
+                or loglik.device != dev:
+            raise ValueError(f"loglik must be contiguous float64 on {dev} with >= {iters} elements")
     return int(lib.fca_em_fast_noalloc(M, F, N, _ptr(y), _ptr(v0), _ptr(S0), int(iters), _ptr(v),
                                        _ptr(x1), _ptr(x2), _ptr(loglik),
                                        ctypes.c_void_p(_stream(stream))))

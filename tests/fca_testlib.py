@@ -18,9 +18,12 @@ import torch
 TOL_MED, TOL_MAX, TOL_LL = 1e-4, 1e-3, 1e-6
 
 
-def gpu_run(form, y, v0, S0, iters, y16=None, g=None, mode=0, host=False, want_S=True):
+def gpu_run(form, y, v0, S0, iters, y16=None, g=None, mode=0, host=False, want_S=True,
+            precision=None, max_sweeps=30):
     """Run one EM on the GPU through the binding. y: complex64 numpy [F,N,M] (or None when
-    y16/g are given). Returns numpy arrays (v, S, mu1, mu2, ll, llf) and the status code."""
+    y16/g are given); precision: None (the library default) or FCA_GEVD_FP32 / FCA_GEVD_FP64.
+    Returns numpy arrays (v, S, mu1, mu2, ll, llf), the status code and the fused kernel's
+    time (kernel_ms)."""
     from paper_1805_06572_gb300 import fca
 
     dev = torch.device("cuda")
@@ -39,6 +42,9 @@ def gpu_run(form, y, v0, S0, iters, y16=None, g=None, mode=0, host=False, want_S
         yt, v0t, S0t = yt.to(dev), v0t.to(dev), S0t.to(dev)
         gt = gt.to(dev) if gt is not None else None
     st = fca.fca_init(yt, v0t, S0t, y_scale=gt)
+    assert precision is not None or max_sweeps == 30, "a sweep cap goes with a precision"
+    if precision is not None:
+        fca.fca_set_eigensolver(st, precision, max_sweeps)
     F, N, M = st.F, st.N, st.M
     ll = torch.empty(max(iters, 1), dtype=torch.float64, device=dev)
     if iters > 0:
@@ -54,6 +60,7 @@ def gpu_run(form, y, v0, S0, iters, y16=None, g=None, mode=0, host=False, want_S
            "ll": ll.cpu().numpy()[:iters], "status": code,
            "S": S.numpy() if S is not None else None}
     out["llf"] = fca.fca_loglik_bins(st).numpy().copy() if iters > 0 and code == 0 else None
+    out["kernel_ms"] = fca.fca_last_em_kernel_ms(st) if iters > 0 and code == 0 else None
     fca.fca_free(st)
     return out
 
