@@ -157,8 +157,10 @@ fca_status fca_sync_status(fca_state* s, void* cuda_stream);
  *                     (one Newton-type correction step, two after a poor start).
  * In the FP64 and refined modes the next basis P Q is formed in FP64 before it is rounded for
  * the bin pass. The bin pass is FP32 and the basis P, log-likelihood and log det S2 are kept
- * in FP64 in every mode. Batches (fca_batch_*) run the FP32 mode. */
+ * in FP64 in every mode. Batches (fca_batch_*) run the FP32 or the refined mode. */
 enum { FCA_GEVD_FP32 = 0, FCA_GEVD_FP64 = 1, FCA_GEVD_REFINED = 2 };
+#define FCA_GEVD_DEFAULT FCA_GEVD_REFINED /* of new states, batches, server requests and
+                                             fca_em_fast_noalloc */
 #define FCA_MAX_SWEEPS_LIMIT 1000
 
 /* Set the eigensolver precision (FCA_GEVD_FP32, _FP64 or _REFINED) and its cap on Jacobi sweeps
@@ -291,15 +293,16 @@ fca_status fca_batch_run(fca_batch* b, int32_t form, int32_t iters, double* logl
                          void* x1_dev, void* x2_dev, float* v_dev, int32_t use_graph,
                          void* cuda_stream);
 
-/* Autotune the FastFCA launch shape of every channel-count group: threads per CTA (64, 128,
- * 256) and how much shared memory a CTA may take to keep its bin's mixture and source powers
+/* Autotune the FastFCA launch shape of every channel-count group: threads per CTA (64 in the
+ * FP32 eigensolver mode, 128, 256) and how much shared memory a CTA may take to keep its bin's mixture and source powers
  * on chip (bins that do not fit stream them from memory every iteration). Each candidate runs
  * min(iters, 4) iterations on a sample of the group's bins (at most 8192) spanning its range
  * of lengths, four times in turn with the others after a warm-up; the one with the best time
  * is kept. As the groups of a job share the GPU, the tuned set is then checked against the
  * default shapes and against all bins streaming, with whole EM passes of all groups at once,
  * and the fastest set is kept for later runs. Synchronises the stream. Overwrites the EM state (not the
- * loaded inputs), so run it before fca_batch_run, not between a run and the use of its outputs. */
+ * loaded inputs) and clears the status word (the timing runs' own status is not a result), so run it
+ * before fca_batch_run, not between a run and the use of its outputs. */
 fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* cuda_stream);
 
 /* Launch shape of the channel-count group M: its number of bins, threads per CTA and the
@@ -308,9 +311,29 @@ fca_status fca_batch_shape(const fca_batch* b, int32_t M, int32_t* bins, int32_t
                            int32_t* res_bytes);
 
 /* Set the launch shape of the channel-count group M (e.g. to reuse shapes tuned earlier):
- * threads per CTA 64, 128 or 256, and res_bytes (0..200 KB) of dynamic shared memory per CTA,
+ * threads per CTA 64 (FP32 eigensolver only), 128 or 256, and res_bytes (0..200 KB) of
+ * dynamic shared memory per CTA,
  * bins needing at most that staying on chip. FCA_ERR_ARG if no mixture has M channels. */
 fca_status fca_batch_set_shape(fca_batch* b, int32_t M, int32_t threads, int32_t res_bytes);
+
+/* Parameters of mixture k (0 <= k < count) after the last fca_batch_run, into host memory:
+ *   S_host    NULL or complex128 [2][F_k][M_k][M_k]: S_j(f) (FastFCA: formed from (P, Lambda)
+ *             by Eqs. (Sdiag), (recoverS); conventional: the last M-step's S_j, Eq. (Supdate));
+ *   llf_host  NULL or double [L][F_k], L the last run's iteration count: entry (l, f) is the
+ *             Eq. (like) term of bin f summed over the mixture's frames at the parameters of
+ *             iteration l (the batch's per-mixture log-likelihood is its sum over f).
+ * Synchronises the stream; FCA_ERR_STATE before any run (or, for llf_host, after a run of
+ * zero iterations). The FastFCA form allocates a temporary of 32 F_g M_k^2 bytes for the
+ * channel-count group's F_g bins. */
+fca_status fca_batch_get_params(fca_batch* b, int32_t k, double* S_host, double* llf_host,
+                                void* cuda_stream);
+
+/* Eigensolver precision of the batch's FastFCA runs (FCA_GEVD_FP32 or FCA_GEVD_REFINED; see
+ * fca_set_eigensolver) and its Jacobi sweep cap (0..FCA_MAX_SWEEPS_LIMIT). A new batch has the
+ * library default. The refined mode runs 128 or 256 threads per CTA (fca_batch_set_shape
+ * refuses 64 there). Changing the precision resets the launch shapes to the defaults (tune
+ * again) and drops the captured graph. Host only. */
+fca_status fca_batch_set_eigensolver(fca_batch* b, int32_t precision, int32_t max_sweeps);
 
 /* Synchronise the stream and return the first device-side error of this batch. After an
  * error every run returns FCA_ERR_STATE until fca_batch_load. */
@@ -349,6 +372,7 @@ typedef struct {
   void* x1;              /* out: complex64 [F][N][M], posterior means of Algorithm 1's output    */
   void* x2;
   double* loglik;        /* out: NULL or double [iters], Eq. (like) at each iteration's parameters */
+  float* v;              /* out: NULL or float [2][F][N], the source powers after the last iteration */
 } fca_request;           /* every buffer is the caller's and must stay valid until the wait returns */
 
 typedef struct {

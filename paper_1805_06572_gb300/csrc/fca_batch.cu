@@ -139,6 +139,9 @@ struct fca_batch {
   int graph_kernels = 0;
   int loaded = 0;
   int failed = 0;
+  int gevd_mode = kDefaultGevdMode;  // FCA_GEVD_FP32 or FCA_GEVD_REFINED
+  int max_sweeps = kDefaultSweeps;
+  int last_form = -1, last_iters = 0;  // of the last fca_batch_run
 };
 
 namespace {
@@ -213,8 +216,8 @@ FastEmArgs fast_args(fca_batch* b, BatchClass& c, int iters, const BinDesc* bins
   a.logdetS2_prev = c.ldet_prev;
   a.llf = c.llf;
   a.status = b->status;
-  a.max_sweeps = kDefaultSweeps;
-  a.gevd_mode = 0;  // the batch kernels run the FP32 eigensolver
+  a.max_sweeps = b->max_sweeps;
+  a.gevd_mode = b->gevd_mode;
   return a;
 }
 
@@ -223,9 +226,16 @@ ParamArgs param_args(fca_batch* b, BatchClass& c) {
   std::memset(&a, 0, sizeof(a));
   a.F = c.nbins;
   a.status = b->status;
-  a.max_sweeps = kDefaultSweeps;
-  a.gevd_mode = 0;
+  a.max_sweeps = b->max_sweeps;
+  a.gevd_mode = b->gevd_mode;
   return a;
+}
+
+// Threads per CTA the fused FastFCA kernel of a batch supports in the current mode (the
+// refined mode needs three warps).
+bool batch_threads_ok(const fca_batch* b, int threads) {
+  if (threads == 128 || threads == 256) return true;
+  return threads == 64 && b->gevd_mode == FCA_GEVD_FP32;
 }
 
 // Enqueue the whole job on `st` (classes forked onto their own streams and joined back).
@@ -515,6 +525,8 @@ fca_status fca_batch_run(fca_batch* b, int32_t form, int32_t iters, double* logl
   if (v_dev && !on_device(v_dev, b->device)) return FCA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   for (BatchClass& c : b->cls) B_CHECK(ensure_llf(c, iters > 0 ? iters : 1));
+  b->last_form = form;
+  b->last_iters = iters;
   if (!use_graph) {
     int nk = 0;
     B_CHECK(enqueue_job(b, form, iters, loglik_dev, x1_dev, x2_dev, v_dev, st, &nk));
@@ -602,6 +614,7 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* stream) {
     const int threads[] = {64, 128, 256};
     const size_t caps[] = {0, 48 * 1024, 100 * 1024, 200 * 1024};
     for (int nt : threads) {
+      if (!batch_threads_ok(b, nt)) continue;
       std::vector<int> tried;
       for (size_t cap : caps) {
         const int rb = resident_bytes(c, cap);
@@ -696,6 +709,14 @@ fca_status fca_batch_tune(fca_batch* b, int32_t iters, void* stream) {
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   drop_graph(b);
+  // The timing runs continue the EM of the sample from one candidate to the next, far past
+  // the iterations asked for; what they record in the status word is not a result of the
+  // batch, so it is cleared (fca_batch_run starts again from the loaded inputs).
+  if (rc == FCA_OK) {
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaMemsetAsync(b->status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = FCA_ERR_CUDA;
+  }
   return rc;
 }
 
@@ -713,8 +734,7 @@ fca_status fca_batch_shape(const fca_batch* b, int32_t M, int32_t* bins, int32_t
 }
 
 fca_status fca_batch_set_shape(fca_batch* b, int32_t M, int32_t threads, int32_t res_bytes) {
-  if (!b || (threads != 64 && threads != 128 && threads != 256) || res_bytes < 0 ||
-      res_bytes > 200 * 1024)
+  if (!b || !batch_threads_ok(b, threads) || res_bytes < 0 || res_bytes > 200 * 1024)
     return FCA_ERR_ARG;
   for (BatchClass& c : b->cls) {
     if (c.M != M) continue;
@@ -724,6 +744,77 @@ fca_status fca_batch_set_shape(fca_batch* b, int32_t M, int32_t threads, int32_t
     return FCA_OK;
   }
   return FCA_ERR_ARG;
+}
+
+fca_status fca_batch_get_params(fca_batch* b, int32_t k, double* S_host, double* llf_host,
+                                void* stream) {
+  if (!b || k < 0 || k >= b->count || (!S_host && !llf_host)) return FCA_ERR_ARG;
+  if (b->failed || b->last_form < 0) return FCA_ERR_STATE;
+  if (llf_host && b->last_iters <= 0) return FCA_ERR_STATE;
+  DeviceGuard guard(b->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  BatchClass* cp = nullptr;
+  int li = -1;
+  for (BatchClass& c : b->cls) {
+    for (size_t i = 0; i < c.mix.size(); ++i)
+      if (c.mix[i] == k) {
+        cp = &c;
+        li = (int)i;
+      }
+  }
+  if (!cp) return FCA_ERR_ARG;
+  BatchClass& c = *cp;
+  const size_t Fk = (size_t)b->F[k], MM = (size_t)c.M * c.M, b0 = (size_t)c.b0[li];
+  if (S_host) {
+    // conventional: the last M-step's S (the initial S0 after a run of zero iterations)
+    const double2* src = b->last_iters > 0 ? c.S : c.S0;
+    double2* tmp = nullptr;
+    if (b->last_form == FCA_FORM_FAST) {  // S_j = P^-H T_j P^-1 of the class's bins
+      B_CHECK(balloc(&tmp, 2 * (size_t)c.nbins * MM));
+      ParamArgs pa = param_args(b, c);
+      pa.P = c.P;
+      pa.lam = c.lam;
+      pa.S_out = tmp;
+      const cudaError_t e = launch_S_from_P(c.M, pa, st);
+      if (e != cudaSuccess) {
+        cudaFree(tmp);
+        return cuda_status(e);
+      }
+      note_launches(1);
+      src = tmp;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+      e = cudaMemcpyAsync(S_host + 2 * (size_t)j * Fk * MM, src + ((size_t)j * c.nbins + b0) * MM,
+                          Fk * MM * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (tmp) cudaFree(tmp);
+    B_CHECK(e);
+  }
+  if (llf_host) {
+    B_CHECK(cudaMemcpy2DAsync(llf_host, Fk * sizeof(double), c.llf + b0, (size_t)c.nbins * sizeof(double),
+                              Fk * sizeof(double), (size_t)b->last_iters, cudaMemcpyDeviceToHost, st));
+    B_CHECK(cudaStreamSynchronize(st));
+  }
+  return FCA_OK;
+}
+
+fca_status fca_batch_set_eigensolver(fca_batch* b, int32_t precision, int32_t max_sweeps) {
+  if (!b || (precision != FCA_GEVD_FP32 && precision != FCA_GEVD_REFINED) || max_sweeps < 0 ||
+      max_sweeps > FCA_MAX_SWEEPS_LIMIT)
+    return FCA_ERR_ARG;
+  if (precision != b->gevd_mode) {
+    // Launch shapes tuned for the other mode no longer apply.
+    for (BatchClass& c : b->cls) {
+      c.threads = 128;
+      c.res_bytes = resident_bytes(c, kResidentCap);
+      c.tuned = 0;
+    }
+  }
+  b->gevd_mode = precision;
+  b->max_sweeps = max_sweeps;
+  drop_graph(b);
+  return FCA_OK;
 }
 
 fca_status fca_batch_sync_status(fca_batch* b, void* stream) {

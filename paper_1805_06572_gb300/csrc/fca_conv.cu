@@ -7,12 +7,12 @@
 //   u = Rx^-1 y, mu_j = v_j S_j u                                  Eq. (MMSE)
 //   C = v1 v2 S1 Rx^-1 S2 = v1 v2 (L^-1 S1)^H (L^-1 S2)            Eq. (postquadexp)
 //   Phi_j = mu_j mu_j^H + C
-//   v_j' = tr(S_j^-1 Phi_j) / M  (old S_j)                         Eq. (vupdate)
+//   v_j' = tr(S_j^-1 Phi_j) / M  (old S_j), as sums of squares     Eq. (vupdate)
 //   Gram_j += Phi_j / v_j'                                          Eq. (Supdate)
 //   log-likelihood term -log det Rx - y^H Rx^-1 y                   Eq. (like)
 // then the CTA merges the Gram partial sums (FP32 warp transpose-reduction, FP64 across
-// warps) and sets S_j' = Gram_j / N in FP64. S_j^-1 for the next v update is formed once per
-// frequency per iteration by warp 0 (FP32 Cholesky of the FP64 S_j).
+// warps) and sets S_j' = Gram_j / N in FP64. The Cholesky factors K_j of S_j for the next v
+// update are formed once per frequency per iteration by warp 0 (FP64 factorisation).
 #include "fca_dev.cuh"
 #include "fca_internal.h"
 
@@ -25,45 +25,32 @@ struct ConvShared {
   double tot[V];
   double2 S[2][kMaxM][kMaxM];
   float2 S32[2][M][M];
-  float2 Si32[2][M][M];
+  float2 K32[2][M][M];  // S32_j = K_j K_j^H
   int fail;
-  WarpLA la;
+  WarpLAT<double> la;
 };
 
 __host__ __device__ constexpr int cpair_index(int M, int i, int k) {  // i < k
   return i * (M - 1) - i * (i - 1) / 2 + (k - i - 1);
 }
 
-// FP32 inverse of the Hermitian positive definite FP64 matrix S (warp 0): S = L L^H,
-// S^-1 = L^-H L^-1. Returns false if S is not positive definite.
+// The FP32 copy S32 of the FP64 S_j used by the bin pass, and the Cholesky factor K of S32
+// itself (S32 = K K^H; factorised in FP64 from the exact FP32 values, then rounded): warp 0.
+// Returns false if S32 is not positive definite.
 template <int M>
-__device__ bool warp_hpd_inverse(WarpLA& la, const double2 (*S)[kMaxM], float2 (*S32)[M],
-                                 float2 (*Si)[M], int lane) {
+__device__ bool warp_hpd_factor(WarpLAT<double>& la, const double2 (*S)[kMaxM], float2 (*S32)[M],
+                                float2 (*K)[M], int lane) {
   for (int e = lane; e < M * M; e += 32) {
     const int i = e / M, j = e % M;
     const float2 s = z2c(S[i][j]);
-    la.L[i][j] = s;
     S32[i][j] = s;
+    la.L[i][j] = c2z(s);
   }
   __syncwarp();
   if (!warp_cholesky<M>(la, lane)) return false;
-  if (lane < M) {  // Z = L^-1 (column `lane` of the identity)
-    const int c = lane;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      float2 s = make_float2(i == c ? 1.f : 0.f, 0.f);
-#pragma unroll
-      for (int m = 0; m < i; ++m) s = csub(s, cmul(la.L[i][m], la.Z[m][c]));
-      la.Z[i][c] = cscale(s, la.invd[i]);
-    }
-  }
-  __syncwarp();
-  for (int e = lane; e < M * M; e += 32) {  // Si = Z^H Z
+  for (int e = lane; e < M * M; e += 32) {
     const int i = e / M, j = e % M;
-    float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int m = 0; m < M; ++m) s = cadd(s, ccmul(la.Z[m][i], la.Z[m][j]));
-    Si[i][j] = s;
+    K[i][j] = (j <= i) ? z2c(la.L[i][j]) : make_float2(0.f, 0.f);
   }
   __syncwarp();
   return true;
@@ -156,8 +143,8 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
       }
     }
     if (warp == 0) {
-      bool ok = warp_hpd_inverse<M>(sh.la, sh.S[0], sh.S32[0], sh.Si32[0], lane);
-      ok = ok && warp_hpd_inverse<M>(sh.la, sh.S[1], sh.S32[1], sh.Si32[1], lane);
+      bool ok = warp_hpd_factor<M>(sh.la, sh.S[0], sh.S32[0], sh.K32[0], lane);
+      ok = ok && warp_hpd_factor<M>(sh.la, sh.S[1], sh.S32[1], sh.K32[1], lane);
       if (!ok && lane == 0) {
         set_status(a.status, kErrNotPD);
         sh.fail = kErrNotPD;
@@ -264,23 +251,38 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
           C[i][k] = cscale(s, v12);
           if (k == i) C[i][i].y = 0.f;
         }
-      // v_j' = (mu_j^H S_j^-1 mu_j + tr(S_j^-1 C)) / M with the old S_j (Eq. (vupdate)).
-      float t1 = 0.f, t2 = 0.f;
+      // v_j' = (mu_j^H S_j^-1 mu_j + tr(S_j^-1 C)) / M with the old S_j (Eq. (vupdate)), as sums
+      // of squares: mu_j = v_j S_j u gives mu_j^H S_j^-1 mu_j = v_j^2 ||K_j^H u||^2, and
+      // C = v1 v2 S1 Rx^-1 S2 gives tr(S1^-1 C) = v1 v2 ||L^-1 K2||_F^2 and tr(S2^-1 C) =
+      // v1 v2 ||L^-1 K1||_F^2 (Rx = L L^H, S_j = K_j K_j^H): no cancellation, and no S_j^-1.
+      float q1 = 0.f, q2 = 0.f, r1 = 0.f, r2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        t1 += sh.Si32[0][i][i].x * (cabs2(mu1[i]) + C[i][i].x);
-        t2 += sh.Si32[1][i][i].x * (cabs2(mu2[i]) + C[i][i].x);
+      for (int c = 0; c < M; ++c) {
+        float2 a1 = make_float2(0.f, 0.f), a2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = i + 1; k < M; ++k) {
-          // 2 Re(conj(mu_i) Si_ik mu_k) + 2 Re(Si_ik conj(C_ik))
-          const float2 z1 = cmul(sh.Si32[0][i][k], mu1[k]);
-          const float2 z2 = cmul(sh.Si32[1][i][k], mu2[k]);
-          t1 += 2.f * (fmaf(mu1[i].x, z1.x, mu1[i].y * z1.y) +
-                       fmaf(sh.Si32[0][i][k].x, C[i][k].x, sh.Si32[0][i][k].y * C[i][k].y));
-          t2 += 2.f * (fmaf(mu2[i].x, z2.x, mu2[i].y * z2.y) +
-                       fmaf(sh.Si32[1][i][k].x, C[i][k].x, sh.Si32[1][i][k].y * C[i][k].y));
+        for (int r = c; r < M; ++r) {  // (K_j^H u)_c
+          a1 = cfma(cconj(sh.K32[0][r][c]), u[r], a1);
+          a2 = cfma(cconj(sh.K32[1][r][c]), u[r], a2);
+        }
+        q1 += cabs2(a1);
+        q2 += cabs2(a2);
+        float2 x1[M], x2[M];  // column c of L^-1 K_j (zero above row c)
+#pragma unroll
+        for (int i = c; i < M; ++i) {
+          float2 s1 = sh.K32[0][i][c], s2 = sh.K32[1][i][c];
+#pragma unroll
+          for (int k = c; k < i; ++k) {
+            s1 = csub(s1, cmul(L[i][k], x1[k]));
+            s2 = csub(s2, cmul(L[i][k], x2[k]));
+          }
+          x1[i] = cscale(s1, L[i][i].y);
+          x2[i] = cscale(s2, L[i][i].y);
+          r2 += cabs2(x1[i]);
+          r1 += cabs2(x2[i]);
         }
       }
+      const float t1 = v1 * fmaf(v1, q1, v2 * r1);
+      const float t2 = v2 * fmaf(v2, q2, v1 * r2);
       const float v1n = fmaxf(t1 * (1.f / M), vf);
       const float v2n = fmaxf(t2 * (1.f / M), vf);
       v1p[n] = v1n;

@@ -923,11 +923,14 @@ __device__ int warp_gevd_reg(const Cx<T> (*A)[kMaxM], Cx<T> (*B)[kMaxM], T* sig,
 // S = X^H A X, lam_i = s_ii / (1 - r_ii), E_ii = r_ii / 2, E_ij = (s_ij + lam_j r_ij) /
 // (lam_j - lam_i) for i != j, and X <- X (I + E). To first order in R and the off-diagonal
 // part of S this makes X^H B X = I and X^H A X = diag(lam), so the residuals square with each
-// step. A pair whose eigenvalues lie closer than kSep of their size cannot be separated this
-// way and takes E_ij = r_ij / 2 (its invariant subspace is still refined). T1, T2: workspace.
-// Writes lam (the Rayleigh quotients of the incoming X) and returns max_ij |E_ij|_1 (all
-// lanes; NaN propagates). With first = true, X is taken to be the identity (not read): R =
-// I - B and S = A. All 32 lanes; ends with __syncwarp().
+// step, as long as every |E_ij| stays small. A pair (i, j) whose coupling
+// c_ij = s_ij + lam_j r_ij is not below a tenth of its eigenvalue gap cannot be separated this
+// way: if the coupling is negligible (below kSep of the eigenvalues: a degenerate or already
+// resolved pair) it takes E_ij = r_ij / 2, otherwise the step fails and returns +infinity (the
+// caller then takes the Jacobi solver). T1, T2: workspace. Writes lam (the Rayleigh quotients
+// of the incoming X) and returns max_ij |E_ij|_1 (all lanes; NaN propagates). With first =
+// true, X is taken to be the identity (not read): R = I - B and S = A. All 32 lanes; ends with
+// __syncwarp().
 template <int M, typename T>
 __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], Cx<T> (*X)[kMaxM],
                               Cx<T> (*T1)[kMaxM], Cx<T> (*T2)[kMaxM], T* lam, bool first,
@@ -935,7 +938,7 @@ __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], 
   using C = Cx<T>;
   constexpr int MM = M * M;
   constexpr int kPer = (MM + 31) / 32;
-  constexpr T kSep = sizeof(T) == 8 ? T(1e-12) : T(1e-6);
+  constexpr T kSep = sizeof(T) == 8 ? T(1e-13) : T(1e-6);
   if (!first) {
 #pragma unroll
     for (int t = 0; t < kPer; ++t) {  // T1 = B X, T2 = A X
@@ -995,19 +998,24 @@ __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], 
     if (e < MM) {
       const int i = e / M, j = e % M;
       C ev;
+      T m;
       if (i == j) {
         ev = mkc<T>(T(0.5) * r[t].x, T(0));
+        m = absT(ev.x);
       } else {
         const T li = lam[i], lj = lam[j], gap = lj - li;
-        if (absT(gap) > kSep * maxT(absT(li), absT(lj))) {
+        const C cp = mkc<T>(fmaT(lj, r[t].x, sv[t].x), fmaT(lj, r[t].y, sv[t].y));
+        const T cm = absT(cp.x) + absT(cp.y);
+        if (cm <= T(0.1) * absT(gap)) {
           const T rg = rcp_fast(gap);
-          ev = mkc<T>(fmaT(lj, r[t].x, sv[t].x) * rg, fmaT(lj, r[t].y, sv[t].y) * rg);
+          ev = mkc<T>(cp.x * rg, cp.y * rg);
+          m = absT(ev.x) + absT(ev.y);
         } else {
           ev = mkc<T>(T(0.5) * r[t].x, T(0.5) * r[t].y);
+          m = (cm <= kSep * maxT(absT(li), absT(lj))) ? absT(ev.x) + absT(ev.y) : T(INFINITY);
         }
       }
       T1[i][j] = ev;
-      const T m = absT(ev.x) + absT(ev.y);
       emax = (m > emax || m != m) ? m : emax;
     }
   }
@@ -1056,16 +1064,154 @@ struct RefineWork {
   double lam[kMaxM];
 };
 
-// FP64 refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B): Newton-type steps
-// (warp_newton_step) in FP64, one, or two when the first correction exceeded 1e-4 (a poor
-// start); the result is X^H B X = I and X^H A X = diag(lam) to second order in the FP32
-// residuals. Leaves X in w.X and lam in w.lam. All 32 lanes; ends with __syncwarp().
+// One FP64 step of warp_newton_step on w.X for the pencil (w.A, w.B), arranged to spend few
+// FP64 operations (they are the scarce resource on this GPU): the residuals R and S, whose
+// small entries come from cancellation, and lam in FP64; the correction E (a small quantity,
+// needed to a few digits) and the product X E in FP32, added to X in FP64. lam_i =
+// s_ii / (1 - r_ii) is taken to second order in r_ii. A pair whose coupling is not below a
+// tenth of its gap (eigenvalues the FP32 start did not separate further than its own
+// accuracy, a degenerate pair among them) keeps its FP32 rotation: E_ij = r_ij / 2. For
+// M <= 4 the two lanes of each pair split every length-M sum (all 32 lanes busy). Returns
+// max_ij |E_ij|_1 (all lanes).
 template <int M>
-__device__ void warp_refine_gevd(RefineWork& w, const float2 (*X0)[kMaxM], int lane) {
+__device__ double warp_refine_step64(RefineWork& w, float2 (*E)[kMaxM], int lane) {
+  constexpr int MM = M * M;
+  constexpr bool kSplit = MM <= 16;
+  constexpr int kPer = kSplit ? 1 : (MM + 31) / 32;
+  constexpr int kStride = kSplit ? 2 : 1;
+  const int h = kSplit ? (lane & 1) : 0;
+  auto entry = [&](int t) { return kSplit ? (lane >> 1) : lane + 32 * t; };
+  // T1 = B X, T2 = A X
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    const int i = (e < MM) ? e / M : 0, j = (e < MM) ? e % M : 0;
+    double2 b = make_double2(0.0, 0.0), a = make_double2(0.0, 0.0);
+    if (e < MM) {
+#pragma unroll
+      for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+        const int k = kk * kStride + h;
+        if (k < M) {
+          b = zfma(w.B[i][k], w.X[k][j], b);
+          a = zfma(w.A[i][k], w.X[k][j], a);
+        }
+      }
+    }
+    if constexpr (kSplit) {
+      b.x += __shfl_xor_sync(0xffffffffu, b.x, 1);
+      b.y += __shfl_xor_sync(0xffffffffu, b.y, 1);
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, 1);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, 1);
+    }
+    if (e < MM && h == 0) {
+      w.T1[i][j] = b;
+      w.T2[i][j] = a;
+    }
+  }
+  __syncwarp();
+  // R = I - X^H T1, S = X^H T2; lam
+  double2 r[kPer], sv[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    const int i = (e < MM) ? e / M : 0, j = (e < MM) ? e % M : 0;
+    double2 q = make_double2(0.0, 0.0), u = make_double2(0.0, 0.0);
+    if (e < MM) {
+#pragma unroll
+      for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+        const int k = kk * kStride + h;
+        if (k < M) {
+          q = cfma(cconj(w.X[k][i]), w.T1[k][j], q);
+          u = cfma(cconj(w.X[k][i]), w.T2[k][j], u);
+        }
+      }
+    }
+    if constexpr (kSplit) {
+      q.x += __shfl_xor_sync(0xffffffffu, q.x, 1);
+      q.y += __shfl_xor_sync(0xffffffffu, q.y, 1);
+      u.x += __shfl_xor_sync(0xffffffffu, u.x, 1);
+      u.y += __shfl_xor_sync(0xffffffffu, u.y, 1);
+    }
+    r[t] = make_double2((i == j ? 1.0 : 0.0) - q.x, -q.y);
+    sv[t] = u;
+    if (e < MM && h == 0 && i == j) w.lam[i] = fma(u.x, fma(r[t].x, r[t].x, r[t].x), u.x);
+  }
+  __syncwarp();
+  // E (FP32)
+  float emax = 0.f;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    if (e < MM && h == 0) {
+      const int i = e / M, j = e % M;
+      float2 ev;
+      if (i == j) {
+        ev = make_float2((float)(0.5 * r[t].x), 0.f);
+      } else {
+        const double li = w.lam[i], lj = w.lam[j];
+        const float gap = (float)(lj - li);
+        const float cx = (float)fma(lj, r[t].x, sv[t].x), cy = (float)fma(lj, r[t].y, sv[t].y);
+        if (fabsf(cx) + fabsf(cy) <= 0.1f * fabsf(gap)) {
+          const float rg = __fdividef(1.f, gap);
+          ev = make_float2(cx * rg, cy * rg);
+        } else {
+          ev = make_float2((float)(0.5 * r[t].x), (float)(0.5 * r[t].y));
+        }
+      }
+      E[i][j] = ev;
+      const float m = fabsf(ev.x) + fabsf(ev.y);
+      emax = (m > emax || m != m) ? m : emax;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const float other = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = (other > emax || other != other) ? other : emax;
+  }
+  __syncwarp();
+  // X <- X + X E, the product in FP32
+  float2 dx[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    const int i = (e < MM) ? e / M : 0, j = (e < MM) ? e % M : 0;
+    float2 d = make_float2(0.f, 0.f);
+    if (e < MM) {
+#pragma unroll
+      for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+        const int k = kk * kStride + h;
+        if (k < M) d = cfma(z2c(w.X[i][k]), E[k][j], d);
+      }
+    }
+    if constexpr (kSplit) {
+      d.x += __shfl_xor_sync(0xffffffffu, d.x, 1);
+      d.y += __shfl_xor_sync(0xffffffffu, d.y, 1);
+    }
+    dx[t] = d;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    if (e < MM && h == 0) {
+      const int i = e / M, j = e % M;
+      w.X[i][j] = make_double2(w.X[i][j].x + (double)dx[t].x, w.X[i][j].y + (double)dx[t].y);
+    }
+  }
+  __syncwarp();
+  return (double)emax;
+}
+
+// FP64 refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B): Newton-type steps
+// (warp_refine_step64), one, or two when the first correction exceeded 1e-4 (a poor start);
+// the result is X^H B X = I and X^H A X = diag(lam) to second order in the FP32 residuals.
+// Leaves X in w.X and lam in w.lam. E: FP32 workspace. All 32 lanes; ends with __syncwarp().
+template <int M>
+__device__ void warp_refine_gevd(RefineWork& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM], int lane) {
   for (int e = lane; e < M * M; e += 32) w.X[e / M][e % M] = c2z(X0[e / M][e % M]);
   __syncwarp();
   for (int step = 0; step < 2; ++step) {
-    const double em = warp_newton_step<M, double>(w.A, w.B, w.X, w.T1, w.T2, w.lam, false, lane);
+    const double em = warp_refine_step64<M>(w, E, lane);
     if (!(em > 1e-4)) break;  // converged to second order (also leaves on NaN)
   }
 }

@@ -18,8 +18,10 @@ bool fast_threads_batch(int storage, int threads) {
 
 cudaError_t launch_fast_em(int M, int storage, const FastEmArgs& a, cudaStream_t st, int threads) {
   if (a.bins) {
-    if (!fast_threads_batch(storage, threads) || a.gevd_mode) return cudaErrorInvalidValue;
-    return launch_fast_batch_c64(M, a, st, threads);
+    if (!fast_threads_batch(storage, threads)) return cudaErrorInvalidValue;
+    if (a.gevd_mode == 0) return launch_fast_batch_c64(M, a, st, threads);
+    if (a.gevd_mode == 2 && threads != 64) return launch_fast_batch_c64_refined(M, a, st, threads);
+    return cudaErrorInvalidValue;
   }
   if (threads != 128) return cudaErrorInvalidValue;
   if (a.gevd_mode == 1) return launch_fast_single_g64(M, storage, a, st);

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
           em = en;
         }
         if (newton) {
-          warp_refine_gevd<M>(sh.rf, sh.la.V, lane);
+          warp_refine_gevd<M>(sh.rf, sh.la.V, sh.la.Z, lane);
         } else {
           if constexpr (M <= 4) {
             rc = warp_gevd_reg<M, float>(sh.la.A, sh.la.L, sh.rf.sig0, sh.rf.X0, sh.U[b], &ldL,
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
           } else {
             rc = warp_gevd_fast<M, float>(sh.la, lane, sh.rf.sig0, sh.rf.X0, sh.U[b], &ldL, a.max_sweeps);
           }
-          if (rc == kOk) warp_refine_gevd<M>(sh.rf, sh.rf.X0, lane);
+          if (rc == kOk) warp_refine_gevd<M>(sh.rf, sh.rf.X0, sh.la.Z, lane);
         }
         if (rc == kOk) {
           for (int e = lane; e < MM; e += 32) sh.Q[b][e / M][e % M] = sh.rf.X[e / M][e % M];
@@ -692,8 +692,9 @@ cudaError_t launch_fast_nt(int M, const FastEmArgs& a, cudaStream_t st) {
 }
 
 // Defined in fca_fast_tuned.cu: batches (descriptor tables), complex64 storage, 64, 128 or
-// 256 threads per CTA.
+// 256 threads per CTA; in fca_fast_tuned_refined.cu the same in the refined mode (128 or 256).
 cudaError_t launch_fast_batch_c64(int M, const FastEmArgs& a, cudaStream_t st, int threads);
+cudaError_t launch_fast_batch_c64_refined(int M, const FastEmArgs& a, cudaStream_t st, int threads);
 // Defined in fca_fast64.cu (mode 1) and fca_fast_refined.cu (mode 2): one mixture, 128 threads
 // per CTA.
 cudaError_t launch_fast_single_g64(int M, int storage, const FastEmArgs& a, cudaStream_t st);

@@ -8,7 +8,7 @@ namespace fca {
 // Default sweep cap of the Jacobi eigensolver (FCA_ERR_EIG_NOCONV past it) and default
 // precision mode of FastFCA's per-bin eigensolver and Gram merge (FCA_GEVD_* of fca.h).
 constexpr int kDefaultSweeps = 30;
-constexpr int kDefaultGevdMode = 0;
+constexpr int kDefaultGevdMode = 2;  // FCA_GEVD_DEFAULT
 
 // One frequency bin of a batch of mixtures: where its time-frequency points and source
 // powers live, and which entry of the per-bin parameter arrays it owns. A kernel given a

@@ -322,6 +322,7 @@ cudaError_t launch_request(fca_server* s, const fca_request& r, unsigned char* b
     ++nk;
     if (r.loglik) S_TRY(cudaMemcpyAsync(r.loglik, ll, (size_t)it * 8, cudaMemcpyDefault, st));
   }
+  if (r.v) S_TRY(cudaMemcpyAsync(r.v, v, 2 * fn * sizeof(float), cudaMemcpyDefault, st));
   S_TRY(cudaMemcpyAsync(r.x1, x1, fnm * 8, cudaMemcpyDefault, st));
   S_TRY(cudaMemcpyAsync(r.x2, x2, fnm * 8, cudaMemcpyDefault, st));
   S_TRY(cudaMemcpyAsync(&s->status_host[slot], status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -21,6 +21,7 @@ FCA_MEM_DEVICE, FCA_MEM_HOST = 0, 1
 FCA_SEP_ALG1, FCA_SEP_FINAL_PARAMS = 0, 1
 FCA_FORM_FAST, FCA_FORM_CONVENTIONAL = 0, 1
 FCA_GEVD_FP32, FCA_GEVD_FP64, FCA_GEVD_REFINED = 0, 1, 2
+FCA_GEVD_DEFAULT = FCA_GEVD_REFINED
 FCA_MAX_SWEEPS_LIMIT = 1000
 STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NOMEM",
                 4: "FCA_ERR_NOT_PD", 5: "FCA_ERR_EIG_NOCONV", 6: "FCA_ERR_NONFINITE",
@@ -33,7 +34,8 @@ EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em
            "fca_kernel_launches", "fca_set_eigensolver", "fca_measure_peaks",
            "fca_sync_status", "fca_free", "fca_status_string", "fca_version",
            "fca_em_fast_noalloc", "fca_batch_init", "fca_batch_load", "fca_batch_run",
-           "fca_batch_tune", "fca_batch_shape", "fca_batch_set_shape", "fca_batch_sync_status",
+           "fca_batch_tune", "fca_batch_shape", "fca_batch_set_shape", "fca_batch_set_eigensolver",
+           "fca_batch_get_params", "fca_batch_sync_status",
            "fca_batch_free",
            "fca_server_create", "fca_server_request_bytes", "fca_server_submit",
            "fca_server_wait", "fca_server_stats", "fca_server_destroy", "fca_stft_frames",
@@ -61,7 +63,7 @@ class fca_request(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("iters", ctypes.c_int32), ("y", ctypes.c_void_p),
                 ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p), ("x1", ctypes.c_void_p),
-                ("x2", ctypes.c_void_p), ("loglik", ctypes.c_void_p)]
+                ("x2", ctypes.c_void_p), ("loglik", ctypes.c_void_p), ("v", ctypes.c_void_p)]
 
 
 class fca_request_info(ctypes.Structure):
@@ -118,6 +120,10 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_batch_shape.argtypes = [V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.fca_batch_set_shape.argtypes = [V, I, I, I]
     lib.fca_batch_set_shape.restype = ctypes.c_int
+    lib.fca_batch_get_params.argtypes = [V, I, V, V, V]
+    lib.fca_batch_get_params.restype = ctypes.c_int
+    lib.fca_batch_set_eigensolver.argtypes = [V, I, I]
+    lib.fca_batch_set_eigensolver.restype = ctypes.c_int
     lib.fca_batch_sync_status.argtypes = [V, V]
     lib.fca_batch_free.argtypes = [V]
     lib.fca_batch_free.restype = None
@@ -432,6 +438,23 @@ def fca_batch_set_shape(batch: Batch, M: int, threads: int, res_bytes: int):
                                    int(res_bytes)), "fca_batch_set_shape")
 
 
+def fca_batch_get_params(batch: Batch, k: int, want_S: bool = True, want_llf: bool = False,
+                         iters: int = 0, stream=None):
+    """Mixture k's S (host complex128 [2,F,M,M]) and per-bin log-likelihood (host float64
+    [iters, F]) after the last batch run; None for the ones not asked for."""
+    M, F = batch.M[k], batch.F[k]
+    S = torch.empty((2, F, M, M), dtype=torch.complex128) if want_S else None
+    llf = torch.empty((iters, F), dtype=torch.float64) if want_llf else None
+    _check(lib.fca_batch_get_params(ctypes.c_void_p(batch.handle), int(k), _ptr(S), _ptr(llf),
+                                    ctypes.c_void_p(_stream(stream))), "fca_batch_get_params")
+    return S, llf
+
+
+def fca_batch_set_eigensolver(batch: Batch, precision: int = FCA_GEVD_DEFAULT, max_sweeps: int = 30):
+    _check(lib.fca_batch_set_eigensolver(ctypes.c_void_p(batch.handle), int(precision), int(max_sweeps)),
+           "fca_batch_set_eigensolver")
+
+
 def fca_batch_sync_status(batch: Batch, stream=None) -> int:
     return int(lib.fca_batch_sync_status(ctypes.c_void_p(batch.handle),
                                          ctypes.c_void_p(_stream(stream))))
@@ -470,17 +493,19 @@ def fca_server_request_bytes(M: int, F: int, N: int, iters: int) -> int:
 
 
 def fca_server_submit(srv: Server, y, v0, S0, x1, x2, iters: int, form: int = FCA_FORM_FAST,
-                      loglik=None) -> int:
+                      loglik=None, v=None) -> int:
     """y complex64 [F,N,M], v0 float64 [2,F,N], S0 complex128 [2,F,M,M]; outputs x1, x2
-    complex64 [F,N,M] and loglik float64 [iters] (or None). Host tensors should be pinned."""
+    complex64 [F,N,M], loglik float64 [iters] (or None) and v float32 [2,F,N] (or None). Host
+    tensors should be pinned."""
     F, N, M = y.shape
     r = fca_request(M=M, F=F, N=N, form=int(form), iters=int(iters), y=y.data_ptr(),
                     v0=v0.data_ptr(), S0=S0.data_ptr(), x1=x1.data_ptr(), x2=x2.data_ptr(),
-                    loglik=None if loglik is None else loglik.data_ptr())
+                    loglik=None if loglik is None else loglik.data_ptr(),
+                    v=None if v is None else v.data_ptr())
     t = ctypes.c_uint64()
     _check(lib.fca_server_submit(ctypes.c_void_p(srv.handle), ctypes.byref(r), ctypes.byref(t)),
            "fca_server_submit")
-    srv.live[t.value] = (y, v0, S0, x1, x2, loglik)
+    srv.live[t.value] = (y, v0, S0, x1, x2, loglik, v)
     return t.value
 
 

@@ -228,3 +228,51 @@ def test_results_do_not_depend_on_input_alignment(fca, form, M):
               offset_view(S0, torch.complex128))
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sweep_cap_of_zero_reports_nonconvergence(fca, mode):
+    """A Jacobi sweep cap of 0 set from the host: the eigenproblem of S0, solved again with the
+    new settings at the next fca_em_fast, stops at once and records FCA_ERR_EIG_NOCONV (5) in
+    the status word; the kernels return (nothing waits), the state latches until it is
+    reloaded, and the default cap works again afterwards. Every precision mode."""
+    y, v0, S0 = problem(seed=61, M=4, F=6, N=120)
+    st = fca.fca_init(*to_dev(y, v0, S0))
+    fca.fca_set_eigensolver(st, mode, 0)
+    fca.fca_em_fast(st, 3)
+    assert fca.fca_sync_status(st) == 5  # FCA_ERR_EIG_NOCONV
+    with pytest.raises(fca.FCAError) as e:
+        fca.fca_em_fast(st, 1)
+    assert e.value.code == 8  # FCA_ERR_STATE
+    fca.fca_set_eigensolver(st, mode, 30)
+    fca.fca_load(st, *to_dev(y, v0, S0))
+    fca.fca_em_fast(st, 3)
+    assert fca.fca_sync_status(st) == 0
+
+
+def test_eigensolver_settings_are_checked(fca):
+    y, v0, S0 = problem()
+    st = fca.fca_init(*to_dev(y, v0, S0))
+    for prec, sweeps in ((3, 30), (-1, 30), (0, -1), (2, fca.FCA_MAX_SWEEPS_LIMIT + 1)):
+        with pytest.raises(fca.FCAError) as e:
+            fca.fca_set_eigensolver(st, prec, sweeps)
+        assert e.value.code == 1
+    fca.fca_set_eigensolver(st, fca.FCA_GEVD_FP64, 12)
+    fca.fca_em_fast(st, 2)
+    assert fca.fca_sync_status(st) == 0
+
+
+def test_modes_agree_with_each_other(fca):
+    """The three eigensolver precisions run the same iteration: their results agree to well
+    within the parity tolerances on a well-conditioned problem."""
+    y, v0, S0 = problem(seed=71, M=4, F=12, N=400)
+    F, N, M = y.shape
+    outs = []
+    for mode in (0, 1, 2):
+        st = fca.fca_init(*to_dev(y, v0, S0))
+        fca.fca_set_eigensolver(st, mode, 30)
+        fca.fca_em_fast(st, 10)
+        outs.append(_state_outputs(fca, st, F, N, M))
+    for o in outs[:2]:
+        rel = np.abs(o["v"] - outs[2]["v"]) / outs[2]["v"]
+        assert np.median(rel) < 1e-5 and rel.max() < 1e-3

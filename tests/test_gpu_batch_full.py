@@ -1,6 +1,7 @@
 """The many-mixture workload at full size, in the launch configuration the benchmark times
 (512 mixtures, M in {2,4,6}, N in [200, 6000], F = 513, L = 50; tuned shapes; one CUDA graph
-launch), checked against the FP64 oracle on sampled bins of sampled mixtures. Bins are
+launch), checked against the FP64 oracle on sampled bins of sampled mixtures: v, the
+posterior means, S and the per-bin log-likelihood (read back per mixture). Bins are
 independent EM problems, so the oracle on a bin's own inputs is that bin's exact reference.
 """
 import numpy as np
@@ -39,8 +40,10 @@ def test_full_batch_sampled_bins_match_oracle(full, form):
     x2 = torch.empty_like(x1)
     v = torch.empty(b.v_elems, dtype=torch.float32, device="cuda")
     fid = fca.FCA_FORM_FAST if form == "fast" else fca.FCA_FORM_CONVENTIONAL
-    fca.fca_batch_run(b, fid, L, x1, x2, v=v, use_graph=True)
+    ll = torch.empty(b.count * L, dtype=torch.float64, device="cuda")
+    fca.fca_batch_run(b, fid, L, x1, x2, loglik=ll, v=v, use_graph=True)
     assert fca.fca_batch_sync_status(b) == 0
+    ll = ll.cpu().numpy().reshape(b.count, L)
     fs = np.asarray(SAMPLE_F)
     for k in SAMPLE_MIX:
         M, F, N = b.M[k], b.F[k], b.N[k]
@@ -49,10 +52,13 @@ def test_full_batch_sampled_bins_match_oracle(full, form):
         v0 = p["v0"][vo:vo + 2 * F * N].view(2, F, N)[:, fs].cpu().numpy()
         S0 = p["S0"][so:so + 2 * F * M * M].view(2, F, M, M)[:, fs].cpu().numpy()
         r = oracle.em(form, y, v0, S0, L)
+        S, llf = fca.fca_batch_get_params(b, k, want_llf=True, iters=L)
+        llf = llf.numpy()
+        # The per-bin log-likelihoods add up to the batch's per-mixture total.
+        np.testing.assert_allclose(llf.sum(axis=1), ll[k], rtol=1e-12)
         got = {"mu1": x1[xo:xo + F * N * M].view(F, N, M)[fs].cpu().numpy(),
                "mu2": x2[xo:xo + F * N * M].view(F, N, M)[fs].cpu().numpy(),
                "v": v[vo:vo + 2 * F * N].view(2, F, N)[:, fs].cpu().numpy().astype(np.float64),
-               "S": r["S"], "llf": None}
+               "S": S.numpy()[:, fs], "llf": llf[:, fs]}
         err = errors(got, r, y, fs=np.arange(len(fs)))
-        err.pop("ll", None)
         assert_within(err, f"{form} mixture {k} (M={M}, N={N})")

@@ -40,12 +40,14 @@ def _buffers(torch, y, v0, S0, L):
     return (pin(y.astype(np.complex64)), pin(v0), pin(S0),
             torch.empty((Fy, N, M), dtype=torch.complex64).pin_memory(),
             torch.empty((Fy, N, M), dtype=torch.complex64).pin_memory(),
-            torch.empty(max(L, 1), dtype=torch.float64).pin_memory())
+            torch.empty(max(L, 1), dtype=torch.float64).pin_memory(),
+            torch.empty((2, Fy, N), dtype=torch.float32).pin_memory())
 
 
 def _submit(fca, srv, buf, L, form):
-    y, v0, S0, x1, x2, ll = buf
-    return fca.fca_server_submit(srv, y, v0, S0, x1, x2, L, form=form, loglik=ll if L else None)
+    y, v0, S0, x1, x2, ll, v = buf
+    return fca.fca_server_submit(srv, y, v0, S0, x1, x2, L, form=form, loglik=ll if L else None,
+                                 v=v)
 
 
 @pytest.mark.parametrize("form", ["fast", "conventional"])
@@ -71,11 +73,12 @@ def test_results_in_the_mix_equal_results_alone(env, form):
         for p, q in zip(a[:2], b[3:5]):
             assert np.array_equal(p, q.numpy())
         assert np.array_equal(a[2][:L], b[5].numpy()[:L])
-    # One request of the mix against the oracle.
+        assert np.array_equal(a[3], b[6].numpy())
+    # One request of the mix against the oracle (S is not an output of a request).
     y, v0, S0, L = reqs[4]
     r = oracle.em(form, y, v0, S0, L)
     got = {"mu1": bufs[4][3].numpy(), "mu2": bufs[4][4].numpy(), "ll": bufs[4][5].numpy()[:L],
-           "v": r["v"], "S": r["S"]}
+           "v": bufs[4][6].numpy().astype(np.float64), "S": r["S"]}
     assert_within(errors(got, r, y), form)
     fca.fca_server_destroy(srv)
 
