@@ -34,20 +34,22 @@ namespace fca {
 // Precision modes of the per-bin generalised eigenproblem (FCA_GEVD_* in fca.h):
 //   0  FP32 merge of the Gram partials, FP32 Cholesky + Jacobi, FP32 Q;
 //   1  FP64 merge, FP64 Cholesky + Jacobi, FP64 Q;
-//   2  FP64 merge, FP32 Cholesky + Jacobi, then FP64 refinement of Q (warp_refine_gevd).
+//   2  FP64 merge, FP32 Newton-type iteration (or Cholesky + Jacobi), FP64 refinement of Q.
 template <int GM> struct GevdTypes;
 template <> struct GevdTypes<0> { using Merge = float; using Solve = float; using Out = float; };
 template <> struct GevdTypes<1> { using Merge = double; using Solve = double; using Out = double; };
 template <> struct GevdTypes<2> { using Merge = double; using Solve = float; using Out = double; };
 struct NoRefine {};
 
-template <int M, int NW, int GM>
-struct FastShared {
+// The EM state of one frequency bin in shared memory. NWR: warps whose partial sums the bin
+// pass leaves in red.
+template <int M, int NWR, int GM>
+struct FastBin {
   using Ty = GevdTypes<GM>;
   using SolveT = typename Ty::Solve;
   using OutT = typename Ty::Out;
   static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
-  float red[NW][V];
+  float red[NWR][V];
   double2 P[kMaxM][kMaxM];      // basis P (FP64)
   float2 P32[kMaxM][kMaxM];     // P rounded to FP32
   float2 PH[M][M];              // FP32 P^H (times the decode scale) used by the bin pass
@@ -64,9 +66,32 @@ struct FastShared {
   double logdetS2;
   int fail;          // read by every thread after a barrier; written only before one
   int fail_pending;  // set by the deferred log-likelihood, read after the iteration's barrier
-  int wid0;          // hardware warp slot of warp 0 (chooses the warps' roles)
-  WarpLAT<SolveT> la;
+};
+
+// Workspace of the per-bin eigensolver (one bin at a time).
+template <int GM>
+struct FastWork {
+  WarpLAT<typename GevdTypes<GM>::Solve> la;
   typename std::conditional<GM == 2, RefineWork, NoRefine>::type rf;
+};
+
+template <int M, int NW, int GM>
+struct FastShared : FastBin<M, NW, GM> {
+  int wid0;  // hardware warp slot of warp 0 (chooses the warps' roles)
+  FastWork<GM> w;
+};
+
+// Where one bin's time-frequency points and source powers are, for the bin pass.
+template <int ST>
+struct BinIO {
+  const typename Elem<ST>::T* y;  // the bin's mixture, [N][M] (shared memory or global)
+  float* v1;                      // v_1(., bin), v_2(., bin): working copies
+  float* v2;
+  float* vg1;                     // v_1(., bin) in global memory (v_2 lies dv2 after it)
+  int dv2;
+  ptrdiff_t d_prev;               // v_prev - v
+  int N;
+  float vf, gi;                   // positivity floor, decode scale 1/g_f
 };
 
 // Warp roles of iteration `it`: the eigensolver (and the publication of the next basis), the
@@ -131,7 +156,7 @@ __device__ __forceinline__ void merge_store(C (*D)[kMaxM], int i, int k, int par
   }
 }
 
-// Deferred FP64 bookkeeping of iteration `it`, in two parts that run on two warps at once.
+// Deferred FP64 bookkeeping of iteration `it`, in two parts that may run on two warps at once.
 // Basis part: P <- P Q (Eq. (updatePeff)) and its FP32 copy, Lambda <- Sigma
 // (Eq. (updateLambdaeff)), and at it = L-2 the basis of iteration L-1.
 template <int M, typename Sh>
@@ -175,11 +200,398 @@ __device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int 
   __syncwarp();
 }
 
+// Refined mode, log-likelihood warp: the basis Q of iteration it is St2-orthonormal, so
+// log|det Q|^2 = -log det St2 (from the FP64 Gram, read-only during the tail).
+template <int M, int GM, typename Sh>
+__device__ void fast_logdet(Sh& sh, FastWork<GM>& w, int it, int lane) {
+  if constexpr (GM == 2) {
+    const double ld = warp_logdet_hpd32<M>(w.rf.B, lane);
+    if (lane == 0) sh.ldL[it & 1] = -ld;
+  }
+}
+
+// Load one bin's parameters into its shared state (threads t < MM, M, 1 of the caller's).
+template <int M, typename Sh>
+__device__ void fast_load_params(Sh& sh, const FastEmArgs& a, int f, int t) {
+  constexpr int MM = M * M;
+  if (t < MM) {
+    const double2 p = a.P[(size_t)f * MM + t];
+    sh.P[t / M][t % M] = p;
+    sh.P32[t / M][t % M] = z2c(p);
+  }
+  if (t < M) {
+    const double l = a.lam[(size_t)f * M + t];
+    sh.lam64[t] = l;
+    sh.lam[t] = (float)l;
+    sh.ilam[t] = 1.f / (float)l;
+  }
+  if (t == 0) {
+    sh.logdetS2 = a.logdetS2[f];
+    sh.fail = 0;
+    sh.fail_pending = 0;
+  }
+}
+
+// After fast_load_params (and a barrier): the FP32 P^H of the first pass, and the parameters
+// of iteration L-1 when L = 1.
+template <int M, typename Sh>
+__device__ void fast_first_basis(Sh& sh, const FastEmArgs& a, int f, float gi, int t) {
+  constexpr int MM = M * M;
+  if (t < MM) {
+    const int i = t / M, m = t % M;
+    const double2 p = sh.P[m][i];
+    sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
+  }
+  if (a.iters == 1) {
+    if (t < MM) a.P_prev[(size_t)f * MM + t] = sh.P[t / M][t % M];
+    if (t < M) a.lam_prev[(size_t)f * M + t] = sh.lam64[t];
+    if (t == 0) a.logdetS2_prev[f] = sh.logdetS2;
+  }
+}
+
+// Stage one bin's mixture and initial source powers in shared memory (ys, vs), threads
+// t < nthr of the caller's. Batches (kB) with separate initial values start the working copy
+// of a streaming bin from them instead.
+template <int M, int ST, bool kB>
+__device__ void fast_stage(const typename Elem<ST>::T* yg, typename Elem<ST>::T* ys, float* vs,
+                           float* vg1, int dv2, ptrdiff_t d_in, int N, bool res, int t, int nthr) {
+  using E = typename Elem<ST>::T;
+  if (res) {
+    const size_t bytes = (size_t)N * M * sizeof(E);
+    if ((bytes & 15) == 0 && (!kB || (reinterpret_cast<uintptr_t>(yg) & 15) == 0)) {
+      const uint4* src = reinterpret_cast<const uint4*>(yg);
+      uint4* dst = reinterpret_cast<uint4*>(ys);
+      for (size_t i = t; i < bytes / 16; i += nthr) dst[i] = src[i];
+    } else {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(yg);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(ys);
+      for (size_t i = t; i < bytes / 4; i += nthr) dst[i] = src[i];
+    }
+    for (int n = t; n < N; n += nthr) {
+      vs[n] = vg1[d_in + n];
+      vs[N + n] = vg1[d_in + dv2 + n];
+    }
+  } else if (kB && d_in != 0) {
+    for (int n = t; n < N; n += nthr) {
+      vg1[n] = vg1[d_in + n];
+      vg1[dv2 + n] = vg1[d_in + dv2 + n];
+    }
+  }
+}
+
+// One bin pass (Eqs. (tildey), (MMSEtilde), (updatePhitildeeff), (updateveff),
+// (updateStildeeff) and the Eq. (like) terms, FP32): thread t of nthr (whole warps) takes
+// frames t, t + nthr, ... (M = 8: lane pairs share a frame), updates v, and leaves its warp's
+// partial sums in red_row. last: keep the incoming v as v_prev (the E-step of iteration L-1).
+template <int M, int ST, typename Sh>
+__device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool last, float* red_row,
+                          int lane) {
+  constexpr int MM = M * M;
+  constexpr int V = 2 * MM + 2;
+  constexpr bool kHoist = (M <= 4);
+  // M = 8: a lane pair shares each time-frequency point and lane parity q accumulates Gram q
+  // only (two 8 x 8 Grams per thread, 130 partial sums, do not fit in registers; at M = 7 they
+  // still do, and one lane per point is faster).
+  constexpr bool kPair = (M >= 8);
+  using RS = RedShape<kPair ? MM + 2 : V>;
+  float acc[RS::NA];
+  const int q = kPair ? (lane & 1) : 0;
+#pragma unroll
+  for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
+  float2 ph[kHoist ? M : 1][kHoist ? M : 1];
+  float lamr[M];
+  if constexpr (kHoist) {
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int m = 0; m < M; ++m) ph[i][m] = sh.PH[i][m];
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) lamr[i] = sh.lam[i];
+  const int N = io.N;
+  const float vf = io.vf;
+  float* v1p = io.v1;
+  float* v2p = io.v2;
+
+  for (int n = kPair ? (t >> 1) : t; n < N; n += kPair ? nthr / 2 : nthr) {
+    float2 yv[M];
+    load_bin<M, ST>(io.y + (size_t)n * M, yv);
+    const float v1 = v1p[n], v2 = v2p[n];
+    if (last && q == 0) {
+      io.vg1[io.d_prev + n] = v1;
+      io.vg1[io.d_prev + io.dv2 + n] = v2;
+    }
+    float2 yt[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float2 s;
+      if constexpr (kHoist) {
+        s = cmul(ph[i][0], yv[0]);
+#pragma unroll
+        for (int m = 1; m < M; ++m) s = cfma(ph[i][m], yv[m], s);
+      } else {
+        s = cmul(sh.PH[i][0], yv[0]);
+#pragma unroll
+        for (int m = 1; m < M; ++m) s = cfma(sh.PH[i][m], yv[m], s);
+      }
+      yt[i] = s;
+    }
+    // With r_i = 1/d_i, t_i = lam_i r_i and q_i = |yt_i|^2 r_i^2 (d_i = v1 lam_i + v2):
+    //   v1' = (v1/M)(v1 sum lam_i q_i + v2 sum r_i)     (Eq. (updateveff), j = 1)
+    //   v2' = (v2/M)(v2 sum q_i + v1 sum t_i)           (Eq. (updateveff), j = 2)
+    //   mut1_i / sqrt(v1') = (v1 / sqrt(v1')) t_i yt_i, mut2_i / sqrt(v2') = (v2 / sqrt(v2')) r_i yt_i
+    //   c_i / v_j' = (v1 v2 / v_j') t_i                 (Eq. (updatePhitildeeff))
+    float r[M], tt[M], pp[M];
+    float sA = 0.f, sB = 0.f, sC = 0.f, sD = 0.f, ql = 0.f;
+    LogProd lp;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const float d = fmaf(v1, lamr[i], v2);
+      r[i] = __fdividef(1.f, d);
+      pp[i] = cabs2(yt[i]);
+      tt[i] = lamr[i] * r[i];
+      const float pr = pp[i] * r[i];
+      const float qq = pr * r[i];
+      sA = fmaf(lamr[i], qq, sA);
+      sB += r[i];
+      sC += qq;
+      sD += tt[i];
+      ql += pr;
+      lp.mul(d);
+    }
+    const float v1n = fmaxf((v1 * (1.f / M)) * fmaf(v1, sA, v2 * sB), vf);
+    const float v2n = fmaxf((v2 * (1.f / M)) * fmaf(v2, sC, v1 * sD), vf);
+    if (q == 0) {
+      v1p[n] = v1n;
+      v2p[n] = v2n;
+    }
+    const float rs1 = rsqrtf(v1n), rs2 = rsqrtf(v2n);
+    const float a1 = v1 * rs1, a2 = v2 * rs2;
+    const float v12 = v1 * v2;
+    const float k1 = v12 * (rs1 * rs1), k2 = v12 * (rs2 * rs2);
+    if constexpr (kPair) {
+      // Gram q of this lane: weights s_q,i (s_1,i = a1 t_i, s_2,i = a2 r_i) and k_q.
+      const float kq = q ? k2 : k1;
+      const float aq = q ? a2 : a1;
+      float sq[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        sq[i] = aq * (q ? r[i] : tt[i]);
+        acc[i] = fmaf(sq[i] * sq[i], pp[i], fmaf(kq, tt[i], acc[i]));
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) {
+          const int o = M + 2 * pair_index(M, i, k);
+          const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
+          const float w = sq[i] * sq[k];
+          acc[o] = fmaf(w, z.x, acc[o]);
+          acc[o + 1] = fmaf(w, z.y, acc[o + 1]);
+        }
+      acc[MM] += q ? 0.f : lp.log_fast();
+      acc[MM + 1] += q ? 0.f : ql;
+    } else {
+      float s1[M], s2[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        s1[i] = a1 * tt[i];
+        s2[i] = a2 * r[i];
+        acc[i] = fmaf(s1[i] * s1[i], pp[i], fmaf(k1, tt[i], acc[i]));
+        acc[MM + i] = fmaf(s2[i] * s2[i], pp[i], fmaf(k2, tt[i], acc[MM + i]));
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) {
+          const int o = M + 2 * pair_index(M, i, k);
+          const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
+          const float w1 = s1[i] * s1[k], w2 = s2[i] * s2[k];
+          acc[o] = fmaf(w1, z.x, acc[o]);
+          acc[o + 1] = fmaf(w1, z.y, acc[o + 1]);
+          acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
+          acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
+        }
+      acc[2 * MM] += lp.log_fast();
+      acc[2 * MM + 1] += ql;
+    }
+  }
+  if constexpr (kPair) {
+    warp_reduce_store_pairs<MM>(acc, lane, red_row);
+  } else {
+    warp_reduce_store<V>(acc, lane, red_row);
+  }
+}
+
+// Merge the NWR warp partials of a bin in a fixed order (pairwise): Gram entries in the
+// eigensolver's merge precision (FP32 sums, or the FP32 warp partials summed in FP64) into the
+// solver's work matrices, the two log-likelihood sums with a compensated two-float sum kept in
+// FP64 into llt[b]. Threads t < nthr of the caller's, one value per thread.
+template <int M, int NWR, int GM, typename Sh>
+__device__ void fast_merge(Sh& sh, FastWork<GM>& w, int b, double invN, int t, int nthr) {
+  using MT = typename GevdTypes<GM>::Merge;
+  using ST2 = typename GevdTypes<GM>::Solve;
+  constexpr int MM = M * M;
+  constexpr int V = 2 * MM + 2;
+  for (int e = t; e < V; e += nthr) {
+    if (e < 2 * MM) {
+      MT sv[NWR];
+#pragma unroll
+      for (int k = 0; k < NWR; ++k) sv[k] = (MT)sh.red[k][e];
+#pragma unroll
+      for (int h = 1; h < NWR; h *= 2)
+#pragma unroll
+        for (int k = 0; k + h < NWR; k += 2 * h) sv[k] += sv[k + h];
+      const MT val = sv[0] * (MT)invN;
+      int g, i, k, part;
+      value_entry<M>(e, &g, &i, &k, &part);
+      merge_store<M>(g ? w.la.L : w.la.A, i, k, part, (ST2)val);
+      if constexpr (GM == 2) merge_store<M>(g ? w.rf.B : w.rf.A, i, k, part, (double)val);
+    } else {
+      float hi = sh.red[0][e], lo = 0.f;
+#pragma unroll
+      for (int k = 1; k < NWR; ++k) {  // TwoSum (Knuth): hi + lo = exact running sum
+        const float x = sh.red[k][e];
+        const float s = hi + x;
+        const float bp = s - hi;
+        lo += (hi - (s - bp)) + (x - bp);
+        hi = s;
+      }
+      sh.llt[b][e - 2 * MM] = (double)hi + (double)lo;
+    }
+  }
+}
+
+// The generalised eigenproblem of (St1, St2) of one iteration (Algorithm 1, step 8) on one
+// warp, in the precision of mode GM: Q, Sigma, log|det Q|^2 pieces into
+// slot b. Returns a warp-uniform device status code and records a failure.
+template <int M, int GM, typename Sh>
+__device__ int fast_solve(Sh& sh, FastWork<GM>& w, const FastEmArgs& a, int b, int lane) {
+  using ST2 = typename GevdTypes<GM>::Solve;
+  constexpr int MM = M * M;
+  ST2 ldL = ST2(0);
+  int rc;
+  if constexpr (GM == 2) {
+    // Newton-type iteration from the identity (the basis P already diagonalises the
+    // previous iteration's parameters, so the new Grams are nearly diagonal in it): FP32
+    // steps, then the FP64 refinement against the FP64 Grams. A poor start (a first
+    // correction above 0.1, or steps that do not converge quadratically) takes the FP32
+    // Cholesky + Jacobi solver instead, whose basis the FP64 steps then refine.
+    rc = kOk;
+    float em = warp_newton_step<M, float>(w.la.A, w.la.L, w.la.V, w.la.Z, w.la.A2, w.rf.lam32, true, lane);
+    bool newton = em <= 0.1f;
+    for (int k = 0; newton && em > 1e-5f && k < 4; ++k) {
+      const float en = warp_newton_step<M, float>(w.la.A, w.la.L, w.la.V, w.la.Z, w.la.A2, w.rf.lam32,
+                                                  false, lane);
+      newton = en <= 0.5f * em;
+      em = en;
+    }
+    if (newton) {
+      warp_refine_gevd<M>(w.rf, w.la.V, w.la.Z, lane);
+    } else {
+      if constexpr (M <= 4) {
+        rc = warp_gevd_reg<M, float>(w.la.A, w.la.L, w.rf.sig0, w.rf.X0, sh.U[b], &ldL,
+                                     Prec<float>::kTol, a.max_sweeps, lane);
+      } else {
+        rc = warp_gevd_fast<M, float>(w.la, lane, w.rf.sig0, w.rf.X0, sh.U[b], &ldL, a.max_sweeps);
+      }
+      if (rc == kOk) warp_refine_gevd<M>(w.rf, w.rf.X0, w.la.Z, lane);
+    }
+    if (rc == kOk) {
+      for (int e = lane; e < MM; e += 32) sh.Q[b][e / M][e % M] = w.rf.X[e / M][e % M];
+      if (lane < M) {
+        const double l = w.rf.lam[lane];
+        sh.sig[b][lane] = l;
+        if (!(l > 0.0) || !(l < 1e300)) rc = kErrNotPD;
+      }
+      rc = __reduce_max_sync(0xffffffffu, rc);  // warp-uniform
+    }
+  } else {
+    if constexpr (M <= 4) {
+      rc = warp_gevd_reg<M, ST2>(w.la.A, w.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL,
+                                 Prec<ST2>::kTol, a.max_sweeps, lane);
+    } else {
+      rc = warp_gevd_fast<M, ST2>(w.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL, a.max_sweeps);
+    }
+    if (lane == 0) sh.ldL[b] = ldL;
+  }
+  if (rc != kOk && lane == 0) {
+    set_status(a.status, rc);
+    sh.fail = rc;
+  }
+  return rc;
+}
+
+// Publish the next basis for the bin pass: P^H <- (P Q)^H, from the FP32 copies (FP32
+// eigensolver) or formed in FP64 and then rounded (an FP32 product of the rounded factors loses
+// accuracy in the small columns of an ill-conditioned P), and Lambda <- Sigma. After the
+// deferred basis update of the previous iteration. One warp.
+template <int M, int GM, typename Sh>
+__device__ void fast_publish(Sh& sh, int b, float gi, int lane) {
+  constexpr int MM = M * M;
+  for (int e = lane; e < MM; e += 32) {
+    const int i = e / M, m = e % M;  // (P Q)_{m i}
+    if constexpr (GM != 0) {
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < M; ++k) s = zfma(sh.P[m][k], sh.Q[b][k][i], s);
+      sh.PH[i][m] = make_float2((float)s.x * gi, -(float)s.y * gi);
+    } else {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
+      sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
+    }
+  }
+  if (lane < M) {
+    const float sg = (float)sh.sig[b][lane];
+    sh.lam[lane] = sg;
+    sh.ilam[lane] = 1.f / sg;
+  }
+}
+
+// Write one bin's parameters (and its staged source powers) back to global memory.
+template <int M, int ST, typename Sh>
+__device__ void fast_write_back(Sh& sh, const FastEmArgs& a, int f, const BinIO<ST>& io, bool res,
+                                int t, int nthr) {
+  constexpr int MM = M * M;
+  if (t < MM) a.P[(size_t)f * MM + t] = sh.P[t / M][t % M];
+  if (t < M) a.lam[(size_t)f * M + t] = sh.lam64[t];
+  if (t == 0) a.logdetS2[f] = sh.logdetS2;
+  if (res) {
+    for (int n = t; n < io.N; n += nthr) {
+      io.vg1[n] = io.v1[n];
+      io.vg1[io.dv2 + n] = io.v2[n];
+    }
+  }
+}
+
+// Where bin `slot` of this launch lives: its parameter index f, frames N and element offsets.
+template <int M, bool kB>
+__device__ __forceinline__ void fast_bin_locate(const FastEmArgs& a, int slot, int* f, int* N,
+                                                size_t* yoff, size_t* v1off, size_t* v2off) {
+  if constexpr (kB) {
+    const BinDesc d = a.bins[slot];
+    *f = d.b;
+    *N = d.N;
+    *yoff = (size_t)d.y_off;
+    *v1off = (size_t)d.v1_off;
+    *v2off = (size_t)d.v2_off;
+  } else {
+    *f = slot;
+    *N = a.N;
+    *yoff = (size_t)slot * a.N * M;
+    *v1off = (size_t)slot * a.N;
+    *v2off = (size_t)a.F * a.N + *v1off;
+  }
+}
+
 // kB: the CTA's bin comes from the descriptor table a.bins (a batch); otherwise bin
 // f = blockIdx.x of one mixture with the [F][N][M] / [2][F][N] layouts and v_in == v.
 // GM: precision mode of the per-bin eigensolver and of the cross-warp Gram merge (GevdTypes);
 // the bin pass is FP32 and the basis, log-likelihood and log-determinant bookkeeping FP64 in
-// every mode.
+// every mode. One bin per CTA; per iteration: pass (all warps) -> merge -> eigensolver on one
+// warp while two others do the previous iteration's bookkeeping -> publish.
 template <int M, int ST, int NT, bool kB, int GM = 0>
 __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(const FastEmArgs a) {
   using E = typename Elem<ST>::T;
@@ -187,366 +599,65 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
   static_assert(NW >= 2, "the deferred bookkeeping runs on warp 1");
   static_assert(GM != 2 || NW >= 3, "the refined mode computes log det St2 on a third warp");
   using Sh = FastShared<M, NW, GM>;
-  using MT = typename Sh::Ty::Merge;
-  using ST2 = typename Sh::SolveT;
-  constexpr bool kG64 = GM != 0;  // FP64 basis publication
-  constexpr int V = Sh::V;
-  constexpr int MM = M * M;
-  constexpr bool kHoist = (M <= 4);
-  // M = 8: a lane pair shares each time-frequency point and lane parity q accumulates Gram q
-  // only (two 8 x 8 Grams per thread, 130 partial sums, do not fit in registers; at M = 7 they
-  // still do, and one lane per point is faster).
-  constexpr bool kPair = (M >= 8);
   __shared__ Sh sh;
   extern __shared__ __align__(16) unsigned char dyn[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int f, N;
   size_t yoff, v1off, v2off;
-  if constexpr (kB) {
-    const BinDesc d = a.bins[blockIdx.x];
-    f = d.b;
-    N = d.N;
-    yoff = (size_t)d.y_off;
-    v1off = (size_t)d.v1_off;
-    v2off = (size_t)d.v2_off;
-  } else {
-    f = blockIdx.x;
-    N = a.N;
-    yoff = (size_t)f * N * M;
-    v1off = (size_t)f * N;
-    v2off = (size_t)a.F * N + v1off;
-  }
+  fast_bin_locate<M, kB>(a, blockIdx.x, &f, &N, &yoff, &v1off, &v2off);
   const E* yg = reinterpret_cast<const E*>(a.y) + yoff;
-  float* vg1 = a.v + v1off;
-  const int dv2 = (int)(v2off - v1off);  // v_2(., bin) lies dv2 floats after v_1(., bin)
   // The initial and previous source powers sit at the same offsets in their own arrays; the
   // distances between the arrays are kernel parameters (no registers held in the hot loop).
-  const ptrdiff_t d_in = kB ? a.v_in - a.v : 0, d_prev = a.v_prev - a.v;
+  const ptrdiff_t d_in = kB ? a.v_in - a.v : 0;
   E* ys = reinterpret_cast<E*>(dyn);
   const size_t ybytes = ((size_t)N * M * sizeof(E) + 15) & ~(size_t)15;
   float* vs = reinterpret_cast<float*>(dyn + ybytes);
   // One mixture: the launch reserves exactly its bins' need, or nothing.
   const bool res = kB ? em_bin_smem(M, ST, N) <= (size_t)a.res_bytes : a.res_bytes != 0;
-  const E* ysrc = res ? ys : yg;
-  float* v1p = res ? vs : vg1;
-  float* v2p = res ? vs + N : vg1 + dv2;
-  const float vf = a.vfloor[f];
-  const float gi = (ST == 1) ? a.ginv[f] : 1.f;
+  BinIO<ST> io;
+  io.vg1 = a.v + v1off;
+  io.dv2 = (int)(v2off - v1off);
+  io.d_prev = a.v_prev - a.v;
+  io.y = res ? ys : yg;
+  io.v1 = res ? vs : io.vg1;
+  io.v2 = res ? vs + N : io.vg1 + io.dv2;
+  io.N = N;
+  io.vf = a.vfloor[f];
+  io.gi = (ST == 1) ? a.ginv[f] : 1.f;
   const double invN = 1.0 / (double)N;
 
-  if (tid < MM) {
-    const double2 p = a.P[(size_t)f * MM + tid];
-    sh.P[tid / M][tid % M] = p;
-    sh.P32[tid / M][tid % M] = z2c(p);
-  }
-  if (tid < M) {
-    const double l = a.lam[(size_t)f * M + tid];
-    sh.lam64[tid] = l;
-    sh.lam[tid] = (float)l;
-    sh.ilam[tid] = 1.f / (float)l;
-  }
+  fast_load_params<M>(sh, a, f, tid);
   if (tid == 0) {
-    sh.logdetS2 = a.logdetS2[f];
-    sh.fail = 0;
-    sh.fail_pending = 0;
     unsigned wslot;
     asm volatile("mov.u32 %0, %%warpid;" : "=r"(wslot));
     sh.wid0 = (int)wslot;
   }
-  if (res) {
-    const size_t bytes = (size_t)N * M * sizeof(E);
-    if ((bytes & 15) == 0 && (!kB || (reinterpret_cast<uintptr_t>(yg) & 15) == 0)) {
-      const uint4* src = reinterpret_cast<const uint4*>(yg);
-      uint4* dst = reinterpret_cast<uint4*>(ys);
-      for (size_t i = tid; i < bytes / 16; i += NT) dst[i] = src[i];
-    } else {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(yg);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(ys);
-      for (size_t i = tid; i < bytes / 4; i += NT) dst[i] = src[i];
-    }
-    for (int n = tid; n < N; n += NT) {
-      vs[n] = vg1[d_in + n];
-      vs[N + n] = vg1[d_in + dv2 + n];
-    }
-  } else if (kB && d_in != 0) {
-    // Streaming bin with separate initial values: start the working copy from them (each
-    // thread copies the frames it updates in the iterations below).
-    for (int n = tid; n < N; n += NT) {
-      vg1[n] = vg1[d_in + n];
-      vg1[dv2 + n] = vg1[d_in + dv2 + n];
-    }
-  }
+  fast_stage<M, ST, kB>(yg, ys, vs, io.vg1, io.dv2, d_in, N, res, tid, NT);
   __syncthreads();
-  if (tid < MM) {
-    const int i = tid / M, m = tid % M;
-    const double2 p = sh.P[m][i];
-    sh.PH[i][m] = make_float2((float)p.x * gi, -(float)p.y * gi);
-  }
-  if (a.iters == 1) {  // the parameters of iteration L-1 are the initial ones
-    if (tid < MM) a.P_prev[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
-    if (tid < M) a.lam_prev[(size_t)f * M + tid] = sh.lam64[tid];
-    if (tid == 0) a.logdetS2_prev[f] = sh.logdetS2;
-  }
+  fast_first_basis<M>(sh, a, f, io.gi, tid);
   __syncthreads();
 
   int done = 0;  // iterations whose bin pass and eigensolve completed
   for (int it = 0; it < a.iters; ++it) {
-    const bool last = (it == a.iters - 1);
     const int b = it & 1;
-    using RS = RedShape<kPair ? MM + 2 : V>;
-    float acc[RS::NA];
-    const int q = kPair ? (lane & 1) : 0;
-#pragma unroll
-    for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
-    float2 ph[kHoist ? M : 1][kHoist ? M : 1];
-    float lamr[M], ilamr[M];
-    if constexpr (kHoist) {
-#pragma unroll
-      for (int i = 0; i < M; ++i)
-#pragma unroll
-        for (int m = 0; m < M; ++m) ph[i][m] = sh.PH[i][m];
-    }
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      lamr[i] = sh.lam[i];
-      ilamr[i] = sh.ilam[i];
-    }
-
-    for (int n = kPair ? (tid >> 1) : tid; n < N; n += kPair ? NT / 2 : NT) {
-      float2 yv[M];
-      load_bin<M, ST>(ysrc + (size_t)n * M, yv);
-      const float v1 = v1p[n], v2 = v2p[n];
-      if (last && q == 0) {
-        vg1[d_prev + n] = v1;
-        vg1[d_prev + dv2 + n] = v2;
-      }
-      float2 yt[M];
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        float2 s;
-        if constexpr (kHoist) {
-          s = cmul(ph[i][0], yv[0]);
-#pragma unroll
-          for (int m = 1; m < M; ++m) s = cfma(ph[i][m], yv[m], s);
-        } else {
-          s = cmul(sh.PH[i][0], yv[0]);
-#pragma unroll
-          for (int m = 1; m < M; ++m) s = cfma(sh.PH[i][m], yv[m], s);
-        }
-        yt[i] = s;
-      }
-      // With r_i = 1/d_i, t_i = lam_i r_i and q_i = |yt_i|^2 r_i^2 (d_i = v1 lam_i + v2):
-      //   v1' = (v1/M)(v1 sum lam_i q_i + v2 sum r_i)     (Eq. (updateveff), j = 1)
-      //   v2' = (v2/M)(v2 sum q_i + v1 sum t_i)           (Eq. (updateveff), j = 2)
-      //   mut1_i / sqrt(v1') = (v1 / sqrt(v1')) t_i yt_i, mut2_i / sqrt(v2') = (v2 / sqrt(v2')) r_i yt_i
-      //   c_i / v_j' = (v1 v2 / v_j') t_i                 (Eq. (updatePhitildeeff))
-      float r[M], t[M], pp[M];
-      float sA = 0.f, sB = 0.f, sC = 0.f, sD = 0.f, ql = 0.f;
-      LogProd lp;
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        const float d = fmaf(v1, lamr[i], v2);
-        r[i] = __fdividef(1.f, d);
-        pp[i] = cabs2(yt[i]);
-        t[i] = lamr[i] * r[i];
-        const float pr = pp[i] * r[i];
-        const float q = pr * r[i];
-        sA = fmaf(lamr[i], q, sA);
-        sB += r[i];
-        sC += q;
-        sD += t[i];
-        ql += pr;
-        lp.mul(d);
-      }
-      const float v1n = fmaxf((v1 * (1.f / M)) * fmaf(v1, sA, v2 * sB), vf);
-      const float v2n = fmaxf((v2 * (1.f / M)) * fmaf(v2, sC, v1 * sD), vf);
-      if (q == 0) {
-        v1p[n] = v1n;
-        v2p[n] = v2n;
-      }
-      const float rs1 = rsqrtf(v1n), rs2 = rsqrtf(v2n);
-      const float a1 = v1 * rs1, a2 = v2 * rs2;
-      const float v12 = v1 * v2;
-      const float k1 = v12 * (rs1 * rs1), k2 = v12 * (rs2 * rs2);
-      if constexpr (kPair) {
-        // Gram q of this lane: weights s_q,i (s_1,i = a1 t_i, s_2,i = a2 r_i) and k_q.
-        const float kq = q ? k2 : k1;
-        const float aq = q ? a2 : a1;
-        float sq[M];
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          sq[i] = aq * (q ? r[i] : t[i]);
-          acc[i] = fmaf(sq[i] * sq[i], pp[i], fmaf(kq, t[i], acc[i]));
-        }
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-#pragma unroll
-          for (int k = i + 1; k < M; ++k) {
-            const int o = M + 2 * pair_index(M, i, k);
-            const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
-            const float w = sq[i] * sq[k];
-            acc[o] = fmaf(w, z.x, acc[o]);
-            acc[o + 1] = fmaf(w, z.y, acc[o + 1]);
-          }
-        acc[MM] += q ? 0.f : lp.log_fast();
-        acc[MM + 1] += q ? 0.f : ql;
-      } else {
-        float s1[M], s2[M];
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          s1[i] = a1 * t[i];
-          s2[i] = a2 * r[i];
-          acc[i] = fmaf(s1[i] * s1[i], pp[i], fmaf(k1, t[i], acc[i]));
-          acc[MM + i] = fmaf(s2[i] * s2[i], pp[i], fmaf(k2, t[i], acc[MM + i]));
-        }
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-#pragma unroll
-          for (int k = i + 1; k < M; ++k) {
-            const int o = M + 2 * pair_index(M, i, k);
-            const float2 z = cmulc(yt[i], yt[k]);  // yt_i conj(yt_k)
-            const float w1 = s1[i] * s1[k], w2 = s2[i] * s2[k];
-            acc[o] = fmaf(w1, z.x, acc[o]);
-            acc[o + 1] = fmaf(w1, z.y, acc[o + 1]);
-            acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
-            acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
-          }
-        acc[2 * MM] += lp.log_fast();
-        acc[2 * MM + 1] += ql;
-      }
-    }
-
-    if constexpr (kPair) {
-      warp_reduce_store_pairs<MM>(acc, lane, sh.red[warp]);
-    } else {
-      warp_reduce_store<V>(acc, lane, sh.red[warp]);
-    }
+    fast_pass<M, ST>(sh, io, tid, NT, it == a.iters - 1, sh.red[warp], lane);
     __syncthreads();
-    // Merge the warp partials in a fixed order (pairwise): Gram entries in the eigensolver's
-    // precision G (FP32 sums, or the FP32 warp partials summed in FP64), the two
-    // log-likelihood sums with a compensated two-float sum kept in FP64. One value per thread.
-    for (int e = tid; e < V; e += NT) {
-      if (e < 2 * MM) {
-        MT sv[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) sv[w] = (MT)sh.red[w][e];
-#pragma unroll
-        for (int h = NW / 2; h >= 1; h >>= 1)
-#pragma unroll
-          for (int w = 0; w < h; ++w) sv[w] += sv[w + h];
-        const MT val = sv[0] * (MT)invN;
-        int g, i, k, part;
-        value_entry<M>(e, &g, &i, &k, &part);
-        merge_store<M>(g ? sh.la.L : sh.la.A, i, k, part, (ST2)val);
-        if constexpr (GM == 2) merge_store<M>(g ? sh.rf.B : sh.rf.A, i, k, part, (double)val);
-      } else {
-        float hi = sh.red[0][e], lo = 0.f;
-#pragma unroll
-        for (int w = 1; w < NW; ++w) {  // TwoSum (Knuth): hi + lo = exact running sum
-          const float x = sh.red[w][e];
-          const float t = hi + x;
-          const float bp = t - hi;
-          lo += (hi - (t - bp)) + (x - bp);
-          hi = t;
-        }
-        sh.llt[b][e - 2 * MM] = (double)hi + (double)lo;
-      }
-    }
+    fast_merge<M, NW, GM>(sh, sh.w, b, invN, tid, NT);
     __syncthreads();
-
     const int ws = solver_warp<NW>(it, sh.wid0);  // eigensolver; then basis, log-likelihood
     const int wb = (ws + 1) % NW, wl = (ws + 2) % NW;
     if (warp == ws) {
-      ST2 ldL = ST2(0);
-      int rc;
-      if constexpr (GM == 2) {
-        // Newton-type iteration from the identity (the basis P already diagonalises the
-        // previous iteration's parameters, so the new Grams are nearly diagonal in it): FP32
-        // steps, then the FP64 refinement against the FP64 Grams. A poor start (a first
-        // correction above 0.1, or steps that do not converge quadratically) takes the FP32
-        // Cholesky + Jacobi solver instead, whose basis the FP64 steps then refine.
-        rc = kOk;
-        float em = warp_newton_step<M, float>(sh.la.A, sh.la.L, sh.la.V, sh.la.Z, sh.la.A2,
-                                              sh.rf.lam32, true, lane);
-        bool newton = em <= 0.1f;
-        for (int k = 0; newton && em > 1e-5f && k < 4; ++k) {
-          const float en = warp_newton_step<M, float>(sh.la.A, sh.la.L, sh.la.V, sh.la.Z, sh.la.A2,
-                                                      sh.rf.lam32, false, lane);
-          newton = en <= 0.5f * em;
-          em = en;
-        }
-        if (newton) {
-          warp_refine_gevd<M>(sh.rf, sh.la.V, sh.la.Z, lane);
-        } else {
-          if constexpr (M <= 4) {
-            rc = warp_gevd_reg<M, float>(sh.la.A, sh.la.L, sh.rf.sig0, sh.rf.X0, sh.U[b], &ldL,
-                                         Prec<float>::kTol, a.max_sweeps, lane);
-          } else {
-            rc = warp_gevd_fast<M, float>(sh.la, lane, sh.rf.sig0, sh.rf.X0, sh.U[b], &ldL, a.max_sweeps);
-          }
-          if (rc == kOk) warp_refine_gevd<M>(sh.rf, sh.rf.X0, sh.la.Z, lane);
-        }
-        if (rc == kOk) {
-          for (int e = lane; e < MM; e += 32) sh.Q[b][e / M][e % M] = sh.rf.X[e / M][e % M];
-          if (lane < M) {
-            const double l = sh.rf.lam[lane];
-            sh.sig[b][lane] = l;
-            if (!(l > 0.0) || !(l < 1e300)) rc = kErrNotPD;
-          }
-          rc = __reduce_max_sync(0xffffffffu, rc);  // warp-uniform
-        }
-      } else {
-        if constexpr (M <= 4) {
-          rc = warp_gevd_reg<M, ST2>(sh.la.A, sh.la.L, sh.sig[b], sh.Q[b], sh.U[b], &ldL,
-                                     Prec<ST2>::kTol, a.max_sweeps, lane);
-        } else {
-          rc = warp_gevd_fast<M, ST2>(sh.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL, a.max_sweeps);
-        }
-        if (lane == 0) sh.ldL[b] = ldL;
-      }
-      if (rc != kOk && lane == 0) {
-        set_status(a.status, rc);
-        sh.fail = rc;
-      }
+      fast_solve<M, GM>(sh, sh.w, a, b, lane);
     } else if (warp == wb && it > 0) {
       fast_deferred_basis<M>(sh, a, f, it - 1, lane);
       if constexpr (NW < 3) fast_deferred_ll<M, GM>(sh, a, f, N, it - 1, lane);
     } else if (NW >= 3 && warp == wl) {
-      // Refined mode: the basis Q of this iteration is St2-orthonormal, so
-      // log|det Q|^2 = -log det St2.
-      if constexpr (GM == 2) {
-        const double ld = warp_logdet_hpd32<M>(sh.rf.B, lane);
-        if (lane == 0) sh.ldL[b] = -ld;
-      }
+      fast_logdet<M, GM>(sh, sh.w, it, lane);
       if (it > 0) fast_deferred_ll<M, GM>(sh, a, f, N, it - 1, lane);
     }
     if (warp == ws || warp == wb) asm volatile("bar.sync 1, 64;" ::: "memory");
-    if (warp == ws) {
-      if (!sh.fail) {
-        // Publish the next basis for the bin pass: P^H <- (P Q)^H, from the FP32 copies (FP32
-        // eigensolver) or in FP64 and then rounded (FP64 eigensolver).
-        for (int e = lane; e < MM; e += 32) {
-          const int i = e / M, m = e % M;  // (P Q)_{m i}
-          if constexpr (kG64) {
-            double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int k = 0; k < M; ++k) s = zfma(sh.P[m][k], sh.Q[b][k][i], s);
-            sh.PH[i][m] = make_float2((float)s.x * gi, -(float)s.y * gi);
-          } else {
-            float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
-            sh.PH[i][m] = make_float2(s.x * gi, -s.y * gi);
-          }
-        }
-        if (lane < M) {
-          const float sg = (float)sh.sig[b][lane];
-          sh.lam[lane] = sg;
-          sh.ilam[lane] = 1.f / sg;
-        }
-      }
-    }
+    if (warp == ws && !sh.fail) fast_publish<M, GM>(sh, b, io.gi, lane);
     __syncthreads();
     if (sh.fail || sh.fail_pending) break;
     done = it + 1;
@@ -560,16 +671,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
     }
   }
   __syncthreads();
-
-  if (tid < MM) a.P[(size_t)f * MM + tid] = sh.P[tid / M][tid % M];
-  if (tid < M) a.lam[(size_t)f * M + tid] = sh.lam64[tid];
-  if (tid == 0) a.logdetS2[f] = sh.logdetS2;
-  if (res) {
-    for (int n = tid; n < N; n += NT) {
-      vg1[n] = vs[n];
-      vg1[dv2 + n] = vs[N + n];
-    }
-  }
+  fast_write_back<M, ST>(sh, a, f, io, res, tid, NT);
 }
 
 // Posterior means in the original basis (Algorithm 1, last step): mu1 = P^-H (a .* yt),
