@@ -344,17 +344,18 @@ template <> struct Prec<double> {
 };
 
 // --------------------------------------------------- warp-level dense Hermitian algebra
-// Matrices are row-major with leading dimension kMaxM, in shared memory. Every function is
-// called by all 32 lanes of one warp and ends with __syncwarp().
-template <typename T>
+// Matrices are row-major with leading dimension kMaxM, in shared memory; a workspace for
+// problems of order at most R holds R rows (an M x M problem reads rows 0..M-1 only). Every
+// function is called by all 32 lanes of one warp and ends with __syncwarp().
+template <typename T, int R = kMaxM>
 struct WarpLAT {
   using C = Cx<T>;
-  C A[kMaxM][kMaxM];   // work matrix (eigenproblem)
-  C L[kMaxM][kMaxM];   // Cholesky factor (lower triangle); L^-1 in the fast solver
-  C Z[kMaxM][kMaxM];   // temporary
-  C V[kMaxM][kMaxM];   // eigenvectors / result
-  C A2[kMaxM][kMaxM];  // ping-pong partners of A and V (fast solver)
-  C V2[kMaxM][kMaxM];
+  C A[R][kMaxM];   // work matrix (eigenproblem)
+  C L[R][kMaxM];   // Cholesky factor (lower triangle); L^-1 in the fast solver
+  C Z[R][kMaxM];   // temporary
+  C V[R][kMaxM];   // eigenvectors / result
+  C A2[R][kMaxM];  // ping-pong partners of A and V (fast solver)
+  C V2[R][kMaxM];
   T invd[kMaxM];       // 1 / L_ii
   C jself[kMaxM + 1];  // Jacobi: J_xx for every index x
   C joth[kMaxM + 1];   // Jacobi: J_{partner(x), x}
@@ -365,8 +366,8 @@ using WarpLA = WarpLAT<float>;
 // In-place Cholesky B = L L^H of the Hermitian positive definite matrix in la.L (the lower
 // triangle is read and overwritten). Returns false (uniformly across the warp) if a pivot is
 // not positive and finite.
-template <int M, typename T>
-__device__ bool warp_cholesky(WarpLAT<T>& la, int lane) {
+template <int M, typename T, int R>
+__device__ bool warp_cholesky(WarpLAT<T, R>& la, int lane) {
   for (int k = 0; k < M; ++k) {
     __syncwarp();
     const T bkk = la.L[k][k].x;
@@ -407,8 +408,8 @@ __device__ bool warp_cholesky(WarpLAT<T>& la, int lane) {
 
 // Lane 0: B (lower triangle of la.L) = L L^H; writes L^-1 (lower, zero above) over la.L and
 // returns log|det L^-H|^2 = 2 sum_i log(1/L_ii). Result is valid on lane 0 only; *ok too.
-template <int M, typename T>
-__device__ T lane_cholesky_inverse(WarpLAT<T>& la, bool* ok) {
+template <int M, typename T, int R>
+__device__ T lane_cholesky_inverse(WarpLAT<T, R>& la, bool* ok) {
   using C = Cx<T>;
   C L[M][M];
   T id[M];
@@ -457,8 +458,8 @@ __device__ T lane_cholesky_inverse(WarpLAT<T>& la, bool* ok) {
 }
 
 // la.A <- W = Li A Li^H (Li = la.L, lower triangular), Hermitian by construction.
-template <int M, typename T>
-__device__ void warp_congruence_products(WarpLAT<T>& la, int lane) {
+template <int M, typename T, int R>
+__device__ void warp_congruence_products(WarpLAT<T, R>& la, int lane) {
   using C = Cx<T>;
   constexpr int kPer = (M * M + 31) / 32;
 #pragma unroll
@@ -509,8 +510,8 @@ __device__ void warp_congruence_products(WarpLAT<T>& la, int lane) {
 // tol relative to sqrt(|a_pp a_qq|) are skipped. Each round reads A/V from one buffer and
 // writes the other; on return the current buffers are la.A / la.V (an even number of swaps is
 // enforced by a final copy when needed). Returns the sweeps taken, or -1 past max_sweeps.
-template <int M, typename T>
-__device__ int warp_jacobi_pp(WarpLAT<T>& la, int lane, T tol, int max_sweeps) {
+template <int M, typename T, int R>
+__device__ int warp_jacobi_pp(WarpLAT<T, R>& la, int lane, T tol, int max_sweeps) {
   using C = Cx<T>;
   using PT = Prec<T>;
   constexpr int n = M + (M & 1);
@@ -666,8 +667,8 @@ __device__ int warp_jacobi_pp(WarpLAT<T>& la, int lane, T tol, int max_sweeps) {
 // *ldL. log|det Q|^2 = *ldL + log|det U|^2, where the rotations leave U unitary only to
 // rounding: log|det U|^2 = ||U||_F^2 - M to first order, which the caller sums in FP64 from
 // Uout (unitarity_defect). Returns a device status code.
-template <int M, typename T>
-__device__ int warp_gevd_fast(WarpLAT<T>& la, int lane, T* sig, Cx<T> (*Qout)[kMaxM],
+template <int M, typename T, int R>
+__device__ int warp_gevd_fast(WarpLAT<T, R>& la, int lane, T* sig, Cx<T> (*Qout)[kMaxM],
                               Cx<T> (*Uout)[kMaxM], T* ldL, int max_sweeps) {
   using C = Cx<T>;
   bool ok = true;
@@ -923,11 +924,13 @@ __device__ int warp_gevd_reg(const Cx<T> (*A)[kMaxM], Cx<T> (*B)[kMaxM], T* sig,
 // S = X^H A X, lam_i = s_ii / (1 - r_ii), E_ii = r_ii / 2, E_ij = (s_ij + lam_j r_ij) /
 // (lam_j - lam_i) for i != j, and X <- X (I + E). To first order in R and the off-diagonal
 // part of S this makes X^H B X = I and X^H A X = diag(lam), so the residuals square with each
-// step, as long as every |E_ij| stays small. A pair (i, j) whose coupling
-// c_ij = s_ij + lam_j r_ij is not below a tenth of its eigenvalue gap cannot be separated this
-// way: if the coupling is negligible (below kSep of the eigenvalues: a degenerate or already
-// resolved pair) it takes E_ij = r_ij / 2, otherwise the step fails and returns +infinity (the
-// caller then takes the Jacobi solver). T1, T2: workspace. Writes lam (the Rayleigh quotients
+// step, as long as every |E_ij| stays small. The two corrections of a pair are set together
+// (by the lane of its upper entry, E_ji = conj(r_ij - E_ij) in either form), so that the first
+// order holds exactly. A pair (i, j) whose couplings c_ij = s_ij + lam_j r_ij and
+// conj(c_ji) = s_ij + lam_i r_ij are not both below a tenth of its eigenvalue gap cannot be
+// separated this way: if they are negligible (below kSep of the eigenvalues: a degenerate or
+// already resolved pair) it takes E_ij = r_ij / 2, otherwise the step fails and returns
+// +infinity (the caller then takes the Jacobi solver). T1, T2: workspace. Writes lam (the Rayleigh quotients
 // of the incoming X) and returns max_ij |E_ij|_1 (all lanes; NaN propagates). With first =
 // true, X is taken to be the identity (not read): R = I - B and S = A. All 32 lanes; ends with
 // __syncwarp().
@@ -997,25 +1000,29 @@ __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], 
     const int e = lane + 32 * t;
     if (e < MM) {
       const int i = e / M, j = e % M;
-      C ev;
-      T m;
+      T m = T(0);
       if (i == j) {
-        ev = mkc<T>(T(0.5) * r[t].x, T(0));
-        m = absT(ev.x);
-      } else {
+        T1[i][i] = mkc<T>(T(0.5) * r[t].x, T(0));
+        m = absT(T(0.5) * r[t].x);
+      } else if (i < j) {  // the pair's upper entry writes both corrections (E_ij + conj(E_ji) = r_ij)
         const T li = lam[i], lj = lam[j], gap = lj - li;
-        const C cp = mkc<T>(fmaT(lj, r[t].x, sv[t].x), fmaT(lj, r[t].y, sv[t].y));
-        const T cm = absT(cp.x) + absT(cp.y);
+        const C c1 = mkc<T>(fmaT(lj, r[t].x, sv[t].x), fmaT(lj, r[t].y, sv[t].y));
+        const C c2 = mkc<T>(fmaT(li, r[t].x, sv[t].x), fmaT(li, r[t].y, sv[t].y));
+        const T cm = maxT(absT(c1.x) + absT(c1.y), absT(c2.x) + absT(c2.y));
+        C eij, eji;
         if (cm <= T(0.1) * absT(gap)) {
           const T rg = rcp_fast(gap);
-          ev = mkc<T>(cp.x * rg, cp.y * rg);
-          m = absT(ev.x) + absT(ev.y);
+          eij = mkc<T>(c1.x * rg, c1.y * rg);
+          eji = mkc<T>(-c2.x * rg, c2.y * rg);
         } else {
-          ev = mkc<T>(T(0.5) * r[t].x, T(0.5) * r[t].y);
-          m = (cm <= kSep * maxT(absT(li), absT(lj))) ? absT(ev.x) + absT(ev.y) : T(INFINITY);
+          eij = mkc<T>(T(0.5) * r[t].x, T(0.5) * r[t].y);
+          eji = cconj(eij);
         }
+        T1[i][j] = eij;
+        T1[j][i] = eji;
+        m = maxT(absT(eij.x) + absT(eij.y), absT(eji.x) + absT(eji.y));
+        if (!(cm <= T(0.1) * absT(gap)) && !(cm <= kSep * maxT(absT(li), absT(lj)))) m = T(INFINITY);
       }
-      T1[i][j] = ev;
       emax = (m > emax || m != m) ? m : emax;
     }
   }
@@ -1051,30 +1058,125 @@ __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], 
   return emax;
 }
 
-// FP64 working arrays of the refined eigensolver (shared memory).
+// ------------------------------------------------- compensated FP32 dot products
+// Error-free transformations in FP32: Knuth's TwoSum (a + b = s + t exactly) and the FMA form
+// of Dekker's TwoProduct (a b = p + e exactly), and the compensated dot product built on them
+// (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005: "Dot2"): the pair (s, c)
+// carries sum_k a_k b_k with an error of order 2^-48 sum_k |a_k b_k| + 2^-24 |result|, as if
+// computed in twice the working precision, on the FP32 pipe. An operand given as a pair
+// (hi, lo) with |lo| <= 2^-24 |hi| (an FP64 value split into two floats) contributes
+// a_k hi_k exactly and a_k lo_k in plain FP32, which keeps the same error order.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = a + b;
+  const float bp = s - a;
+  t = (a - (s - bp)) + (b - bp);
+}
+
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {  // += a b
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    float t;
+    two_sum(s, p, s, t);
+    c += t + e;
+  }
+  __device__ __forceinline__ void add2(float a, float bh, float bl) {  // += a (bh + bl)
+    add(a, bh);
+    c = fmaf(a, bl, c);
+  }
+  __device__ __forceinline__ void merge(const Dot2& o) {  // += o
+    float t;
+    two_sum(s, o.s, s, t);
+    c += t + o.c;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// A complex compensated accumulator: re and im parts.
+struct CDot2 {
+  Dot2 re, im;
+  // += a (bh + bl), complex a and the split complex b
+  __device__ __forceinline__ void fma2(float2 a, float2 bh, float2 bl) {
+    re.add2(a.x, bh.x, bl.x);
+    re.add2(-a.y, bh.y, bl.y);
+    im.add2(a.x, bh.y, bl.y);
+    im.add2(a.y, bh.x, bl.x);
+  }
+  __device__ __forceinline__ double2 value() const { return make_double2(re.value(), im.value()); }
+  __device__ __forceinline__ void shfl_merge(int o) {  // combine with the lane `lane ^ o`
+    Dot2 r, i;
+    r.s = __shfl_xor_sync(0xffffffffu, re.s, o);
+    r.c = __shfl_xor_sync(0xffffffffu, re.c, o);
+    i.s = __shfl_xor_sync(0xffffffffu, im.s, o);
+    i.c = __shfl_xor_sync(0xffffffffu, im.c, o);
+    re.merge(r);
+    im.merge(i);
+  }
+};
+
+// An FP64 complex value split into two complex floats: v = hi + lo, hi = fl32(v).
+__device__ __forceinline__ void split2(double2 v, float2& hi, float2& lo) {
+  hi = z2c(v);
+  lo = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+}
+
+// FP64 working arrays of the refined eigensolver (shared memory), for order at most R.
+template <int R = kMaxM>
 struct RefineWork {
-  double2 A[kMaxM][kMaxM];   // the pencil (A, B) in FP64, B positive definite
-  double2 B[kMaxM][kMaxM];
-  double2 X[kMaxM][kMaxM];   // the basis being refined
-  double2 T1[kMaxM][kMaxM];  // workspace
-  double2 T2[kMaxM][kMaxM];
-  float2 X0[kMaxM][kMaxM];   // the FP32 start (fallback solver's basis)
+  double2 A[R][kMaxM];   // the pencil (A, B) in FP64, B positive definite
+  double2 B[R][kMaxM];
+  float2 Ah[R][kMaxM];   // A and B split into FP32 pairs (hi + lo)
+  float2 Al[R][kMaxM];
+  float2 Bh[R][kMaxM];
+  float2 Bl[R][kMaxM];
+  double2 X[R][kMaxM];   // the basis being refined
+  double2 T1[R][kMaxM];  // workspace
+  double2 T2[R][kMaxM];
+  float2 X0[R][kMaxM];   // the FP32 start (fallback solver's basis)
   float sig0[kMaxM];
   float lam32[kMaxM];
   double lam[kMaxM];
 };
 
+// The corrections of the pair (i, j), i < j, in a refinement step, from the residual entries
+// r = r_ij, s = s_ij and the eigenvalue estimates li, lj: E_ij and E_ji are chosen together,
+// so that E_ij + conj(E_ji) = r_ij holds exactly and X^H B X = I stays true to first order
+// whatever the choice. The Newton form E_ij = c1 / (lj - li), E_ji = -conj(c2) / (lj - li),
+// c1 = lj r + s, c2 = li r + s, is taken when both couplings are below kRefineSep of the gap,
+// so that the second-order terms E^H E are below kRefineSep^2 of the step's residuals;
+// otherwise E_ij = r_ij / 2 (a pair closer than its own coupling: degenerate, or resolved to
+// the start's accuracy, which is all its mixing can affect). Returns max(|E_ij|_1, |E_ji|_1).
+constexpr double kRefineSep = 0.01;
+__device__ __forceinline__ float refine_pair(double li, double lj, double2 r, double2 s, float2* eij,
+                                             float2* eji) {
+  const double gap = lj - li;
+  const float c1x = (float)fma(lj, r.x, s.x), c1y = (float)fma(lj, r.y, s.y);
+  const float c2x = (float)fma(li, r.x, s.x), c2y = (float)fma(li, r.y, s.y);
+  const float cm = fmaxf(fabsf(c1x) + fabsf(c1y), fabsf(c2x) + fabsf(c2y));
+  const float g = (float)gap;
+  if (cm <= (float)kRefineSep * fabsf(g)) {
+    const float rg = __fdividef(1.f, g);
+    *eij = make_float2(c1x * rg, c1y * rg);
+    *eji = make_float2(-c2x * rg, c2y * rg);
+  } else {
+    *eij = make_float2((float)(0.5 * r.x), (float)(0.5 * r.y));
+    *eji = make_float2(eij->x, -eij->y);
+  }
+  return fmaxf(fabsf(eij->x) + fabsf(eij->y), fabsf(eji->x) + fabsf(eji->y));
+}
+
 // One FP64 step of warp_newton_step on w.X for the pencil (w.A, w.B), arranged to spend few
 // FP64 operations (they are the scarce resource on this GPU): the residuals R and S, whose
 // small entries come from cancellation, and lam in FP64; the correction E (a small quantity,
 // needed to a few digits) and the product X E in FP32, added to X in FP64. lam_i =
-// s_ii / (1 - r_ii) is taken to second order in r_ii. A pair whose coupling is not below a
-// tenth of its gap (eigenvalues the FP32 start did not separate further than its own
-// accuracy, a degenerate pair among them) keeps its FP32 rotation: E_ij = r_ij / 2. For
+// s_ii / (1 - r_ii) is taken to second order in r_ii. Each pair's two corrections come from
+// refine_pair (a pair the start did not separate further than its own accuracy, a degenerate
+// pair among them, keeps its rotation: E_ij = r_ij / 2). For
 // M <= 4 the two lanes of each pair split every length-M sum (all 32 lanes busy). Returns
 // max_ij |E_ij|_1 (all lanes).
-template <int M>
-__device__ double warp_refine_step64(RefineWork& w, float2 (*E)[kMaxM], int lane) {
+template <int M, int R>
+__device__ double warp_refine_step64(RefineWork<R>& w, float2 (*E)[kMaxM], int lane) {
   constexpr int MM = M * M;
   constexpr bool kSplit = MM <= 16;
   constexpr int kPer = kSplit ? 1 : (MM + 31) / 32;
@@ -1144,22 +1246,16 @@ __device__ double warp_refine_step64(RefineWork& w, float2 (*E)[kMaxM], int lane
     const int e = entry(t);
     if (e < MM && h == 0) {
       const int i = e / M, j = e % M;
-      float2 ev;
+      float m = 0.f;
       if (i == j) {
-        ev = make_float2((float)(0.5 * r[t].x), 0.f);
-      } else {
-        const double li = w.lam[i], lj = w.lam[j];
-        const float gap = (float)(lj - li);
-        const float cx = (float)fma(lj, r[t].x, sv[t].x), cy = (float)fma(lj, r[t].y, sv[t].y);
-        if (fabsf(cx) + fabsf(cy) <= 0.1f * fabsf(gap)) {
-          const float rg = __fdividef(1.f, gap);
-          ev = make_float2(cx * rg, cy * rg);
-        } else {
-          ev = make_float2((float)(0.5 * r[t].x), (float)(0.5 * r[t].y));
-        }
+        E[i][i] = make_float2((float)(0.5 * r[t].x), 0.f);
+        m = fabsf(E[i][i].x);
+      } else if (i < j) {  // the pair's upper entry writes both corrections
+        float2 eij, eji;
+        m = refine_pair(w.lam[i], w.lam[j], r[t], sv[t], &eij, &eji);
+        E[i][j] = eij;
+        E[j][i] = eji;
       }
-      E[i][j] = ev;
-      const float m = fabsf(ev.x) + fabsf(ev.y);
       emax = (m > emax || m != m) ? m : emax;
     }
   }
@@ -1202,18 +1298,142 @@ __device__ double warp_refine_step64(RefineWork& w, float2 (*E)[kMaxM], int lane
   return (double)emax;
 }
 
-// FP64 refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B): Newton-type steps
-// (warp_refine_step64), one, or two when the first correction exceeded 1e-4 (a poor start);
-// the result is X^H B X = I and X^H A X = diag(lam) to second order in the FP32 residuals.
-// Leaves X in w.X and lam in w.lam. E: FP32 workspace. All 32 lanes; ends with __syncwarp().
-template <int M>
-__device__ void warp_refine_gevd(RefineWork& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM], int lane) {
-  for (int e = lane; e < M * M; e += 32) w.X[e / M][e % M] = c2z(X0[e / M][e % M]);
-  __syncwarp();
-  for (int step = 0; step < 2; ++step) {
-    const double em = warp_refine_step64<M>(w, E, lane);
-    if (!(em > 1e-4)) break;  // converged to second order (also leaves on NaN)
+// The first refinement step from an FP32 basis X0 (exact in FP32): warp_refine_step64 with the
+// residual products on the FP32 pipe. R = I - X0^H B X0 and S = X0^H A X0 are compensated dot
+// products (Dot2) of X0 and the split FP32 pairs of A and B, the inner products B X0 and A X0
+// kept as unrounded pairs; their error is of order 2^-48, the FP64 step's accuracy for this
+// purpose, at no FP64 multiply-add. lam in FP64, the correction E and X0 E in FP32, and
+// X = X0 + X0 E in FP64 (into w.X). Returns max_ij |E_ij|_1 (all lanes).
+template <int M, int R>
+__device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM],
+                                      float2 (*T1h)[kMaxM], float2 (*T1l)[kMaxM],
+                                      float2 (*T2h)[kMaxM], float2 (*T2l)[kMaxM], int lane) {
+  constexpr int MM = M * M;
+  constexpr bool kSplit = MM <= 16;
+  constexpr int kPer = kSplit ? 1 : (MM + 31) / 32;
+  constexpr int kStride = kSplit ? 2 : 1;
+  const int h = kSplit ? (lane & 1) : 0;
+  auto entry = [&](int t) { return kSplit ? (lane >> 1) : lane + 32 * t; };
+  // T1 = B X0, T2 = A X0 as unrounded pairs
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    const int i = (e < MM) ? e / M : 0, j = (e < MM) ? e % M : 0;
+    CDot2 b, a;
+    if (e < MM) {
+#pragma unroll
+      for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+        const int k = kk * kStride + h;
+        if (k < M) {
+          const float2 x = X0[k][j];
+          b.fma2(x, w.Bh[i][k], w.Bl[i][k]);
+          a.fma2(x, w.Ah[i][k], w.Al[i][k]);
+        }
+      }
+    }
+    if constexpr (kSplit) {
+      b.shfl_merge(1);
+      a.shfl_merge(1);
+    }
+    if (e < MM && h == 0) {
+      T1h[i][j] = make_float2(b.re.s, b.im.s);
+      T1l[i][j] = make_float2(b.re.c, b.im.c);
+      T2h[i][j] = make_float2(a.re.s, a.im.s);
+      T2l[i][j] = make_float2(a.re.c, a.im.c);
+    }
   }
+  __syncwarp();
+  // R = I - X0^H T1, S = X0^H T2; lam
+  double2 r[kPer], sv[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    const int i = (e < MM) ? e / M : 0, j = (e < MM) ? e % M : 0;
+    CDot2 q, u;
+    if (e < MM) {
+#pragma unroll
+      for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+        const int k = kk * kStride + h;
+        if (k < M) {
+          const float2 xc = cconj(X0[k][i]);
+          q.fma2(xc, T1h[k][j], T1l[k][j]);
+          u.fma2(xc, T2h[k][j], T2l[k][j]);
+        }
+      }
+    }
+    if constexpr (kSplit) {
+      q.shfl_merge(1);
+      u.shfl_merge(1);
+    }
+    const double2 qv = q.value();
+    r[t] = make_double2((i == j ? 1.0 : 0.0) - qv.x, -qv.y);
+    sv[t] = u.value();
+    if (e < MM && h == 0 && i == j) w.lam[i] = fma(sv[t].x, fma(r[t].x, r[t].x, r[t].x), sv[t].x);
+  }
+  __syncwarp();
+  // E (FP32), as in warp_refine_step64
+  float emax = 0.f;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    if (e < MM && h == 0) {
+      const int i = e / M, j = e % M;
+      float m = 0.f;
+      if (i == j) {
+        E[i][i] = make_float2((float)(0.5 * r[t].x), 0.f);
+        m = fabsf(E[i][i].x);
+      } else if (i < j) {  // the pair's upper entry writes both corrections
+        float2 eij, eji;
+        m = refine_pair(w.lam[i], w.lam[j], r[t], sv[t], &eij, &eji);
+        E[i][j] = eij;
+        E[j][i] = eji;
+      }
+      emax = (m > emax || m != m) ? m : emax;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const float other = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = (other > emax || other != other) ? other : emax;
+  }
+  __syncwarp();
+  // X = X0 + X0 E: the product in FP32, the sum in FP64
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = entry(t);
+    const int i = (e < MM) ? e / M : 0, j = (e < MM) ? e % M : 0;
+    float2 d = make_float2(0.f, 0.f);
+    if (e < MM) {
+#pragma unroll
+      for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+        const int k = kk * kStride + h;
+        if (k < M) d = cfma(X0[i][k], E[k][j], d);
+      }
+    }
+    if constexpr (kSplit) {
+      d.x += __shfl_xor_sync(0xffffffffu, d.x, 1);
+      d.y += __shfl_xor_sync(0xffffffffu, d.y, 1);
+    }
+    if (e < MM && h == 0) {
+      const float2 x0 = X0[i][j];
+      w.X[i][j] = make_double2((double)x0.x + (double)d.x, (double)x0.y + (double)d.y);
+    }
+  }
+  __syncwarp();
+  return (double)emax;
+}
+
+// Refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B): Newton-type steps, the first
+// with compensated FP32 residuals (warp_refine_step_df), a second in FP64
+// (warp_refine_step64) when the first correction exceeded 1e-4 (a poor start); the result is
+// X^H B X = I and X^H A X = diag(lam) to second order in the FP32 residuals. Leaves X in w.X
+// and lam in w.lam. E, T1h..T2l: FP32 workspaces. All 32 lanes; ends with __syncwarp().
+template <int M, int R>
+__device__ void warp_refine_gevd(RefineWork<R>& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM],
+                                 float2 (*T1h)[kMaxM], float2 (*T1l)[kMaxM], float2 (*T2h)[kMaxM],
+                                 float2 (*T2l)[kMaxM], int lane) {
+  const double em = warp_refine_step_df<M>(w, X0, E, T1h, T1l, T2h, T2l, lane);
+  if (em > 1e-4) warp_refine_step64<M>(w, E, lane);
 }
 
 // log det B of a Hermitian positive definite B near the identity (FP64, shared memory), by an

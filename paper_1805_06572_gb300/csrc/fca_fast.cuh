@@ -50,15 +50,18 @@ struct FastBin {
   using OutT = typename Ty::Out;
   static constexpr int V = 2 * M * M + 2;  // two Grams (M^2 reals each), sum log d, sum p/d
   float red[NWR][V];
-  double2 P[kMaxM][kMaxM];      // basis P (FP64)
-  float2 P32[kMaxM][kMaxM];     // P rounded to FP32
+  double2 P[M][kMaxM];      // basis P (FP64); M x M matrices with leading dimension kMaxM
+  float2 P32[M][kMaxM];     // P rounded to FP32
+  float2 P32lo[M][kMaxM];   // P - P32 rounded to FP32 (FP64 modes: the next basis is
+  float2 Qh[M][kMaxM];      //   published from these pairs and Q = Qh + Ql)
+  float2 Ql[M][kMaxM];
   float2 PH[M][M];              // FP32 P^H (times the decode scale) used by the bin pass
   float lam[M], ilam[M];
   double lam64[kMaxM];
   // Double-buffered results of an iteration's eigensolve, consumed by the deferred FP64
   // bookkeeping one iteration later.
-  Cx<OutT> Q[2][kMaxM][kMaxM];
-  Cx<SolveT> U[2][kMaxM][kMaxM];
+  Cx<OutT> Q[2][M][kMaxM];
+  Cx<SolveT> U[2][M][kMaxM];
   OutT sig[2][kMaxM];
   OutT ldL[2];       // modes 0, 1: 2 sum log(1/L_ii), log|det Q|^2 = ldL + log|det U|^2;
                      // mode 2: log|det Q|^2 itself (= -log det St2)
@@ -69,16 +72,16 @@ struct FastBin {
 };
 
 // Workspace of the per-bin eigensolver (one bin at a time).
-template <int GM>
+template <int M, int GM>
 struct FastWork {
-  WarpLAT<typename GevdTypes<GM>::Solve> la;
-  typename std::conditional<GM == 2, RefineWork, NoRefine>::type rf;
+  WarpLAT<typename GevdTypes<GM>::Solve, M> la;
+  typename std::conditional<GM == 2, RefineWork<M>, NoRefine>::type rf;
 };
 
 template <int M, int NW, int GM>
 struct FastShared : FastBin<M, NW, GM> {
   int wid0;  // hardware warp slot of warp 0 (chooses the warps' roles)
-  FastWork<GM> w;
+  FastWork<M, GM> w;
 };
 
 // Where one bin's time-frequency points and source powers are, for the bin pass.
@@ -168,7 +171,7 @@ __device__ void fast_deferred_basis(Sh& sh, const FastEmArgs& a, int f, int it, 
   } else {
     warp_update_basis_q<M>(sh.P, sh.Q[b], lane);
   }
-  for (int e = lane; e < MM; e += 32) sh.P32[e / M][e % M] = z2c(sh.P[e / M][e % M]);
+  for (int e = lane; e < MM; e += 32) split2(sh.P[e / M][e % M], sh.P32[e / M][e % M], sh.P32lo[e / M][e % M]);
   if (lane < M) sh.lam64[lane] = (double)sh.sig[b][lane];
   __syncwarp();
   if (it == a.iters - 2) {  // the parameters of iteration L-1
@@ -203,7 +206,7 @@ __device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int 
 // Refined mode, log-likelihood warp: the basis Q of iteration it is St2-orthonormal, so
 // log|det Q|^2 = -log det St2 (from the FP64 Gram, read-only during the tail).
 template <int M, int GM, typename Sh>
-__device__ void fast_logdet(Sh& sh, FastWork<GM>& w, int it, int lane) {
+__device__ void fast_logdet(Sh& sh, FastWork<M, GM>& w, int it, int lane) {
   if constexpr (GM == 2) {
     const double ld = warp_logdet_hpd32<M>(w.rf.B, lane);
     if (lane == 0) sh.ldL[it & 1] = -ld;
@@ -217,7 +220,7 @@ __device__ void fast_load_params(Sh& sh, const FastEmArgs& a, int f, int t) {
   if (t < MM) {
     const double2 p = a.P[(size_t)f * MM + t];
     sh.P[t / M][t % M] = p;
-    sh.P32[t / M][t % M] = z2c(p);
+    split2(p, sh.P32[t / M][t % M], sh.P32lo[t / M][t % M]);
   }
   if (t < M) {
     const double l = a.lam[(size_t)f * M + t];
@@ -428,7 +431,7 @@ __device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool las
 // solver's work matrices, the two log-likelihood sums with a compensated two-float sum kept in
 // FP64 into llt[b]. Threads t < nthr of the caller's, one value per thread.
 template <int M, int NWR, int GM, typename Sh>
-__device__ void fast_merge(Sh& sh, FastWork<GM>& w, int b, double invN, int t, int nthr) {
+__device__ void fast_merge(Sh& sh, FastWork<M, GM>& w, int b, double invN, int t, int nthr) {
   using MT = typename GevdTypes<GM>::Merge;
   using ST2 = typename GevdTypes<GM>::Solve;
   constexpr int MM = M * M;
@@ -446,7 +449,13 @@ __device__ void fast_merge(Sh& sh, FastWork<GM>& w, int b, double invN, int t, i
       int g, i, k, part;
       value_entry<M>(e, &g, &i, &k, &part);
       merge_store<M>(g ? w.la.L : w.la.A, i, k, part, (ST2)val);
-      if constexpr (GM == 2) merge_store<M>(g ? w.rf.B : w.rf.A, i, k, part, (double)val);
+      if constexpr (GM == 2) {
+        const double dv = (double)val;
+        const float hv = (float)dv, lv = (float)(dv - (double)hv);
+        merge_store<M>(g ? w.rf.B : w.rf.A, i, k, part, dv);
+        merge_store<M>(g ? w.rf.Bh : w.rf.Ah, i, k, part, hv);
+        merge_store<M>(g ? w.rf.Bl : w.rf.Al, i, k, part, lv);
+      }
     } else {
       float hi = sh.red[0][e], lo = 0.f;
 #pragma unroll
@@ -466,7 +475,7 @@ __device__ void fast_merge(Sh& sh, FastWork<GM>& w, int b, double invN, int t, i
 // warp, in the precision of mode GM: Q, Sigma, log|det Q|^2 pieces into
 // slot b. Returns a warp-uniform device status code and records a failure.
 template <int M, int GM, typename Sh>
-__device__ int fast_solve(Sh& sh, FastWork<GM>& w, const FastEmArgs& a, int b, int lane) {
+__device__ int fast_solve(Sh& sh, FastWork<M, GM>& w, const FastEmArgs& a, int b, int lane) {
   using ST2 = typename GevdTypes<GM>::Solve;
   constexpr int MM = M * M;
   ST2 ldL = ST2(0);
@@ -487,7 +496,7 @@ __device__ int fast_solve(Sh& sh, FastWork<GM>& w, const FastEmArgs& a, int b, i
       em = en;
     }
     if (newton) {
-      warp_refine_gevd<M>(w.rf, w.la.V, w.la.Z, lane);
+      warp_refine_gevd<M>(w.rf, w.la.V, w.la.Z, w.la.A2, w.la.V2, w.la.A, w.la.L, lane);  // A, L free now
     } else {
       if constexpr (M <= 4) {
         rc = warp_gevd_reg<M, float>(w.la.A, w.la.L, w.rf.sig0, w.rf.X0, sh.U[b], &ldL,
@@ -495,10 +504,14 @@ __device__ int fast_solve(Sh& sh, FastWork<GM>& w, const FastEmArgs& a, int b, i
       } else {
         rc = warp_gevd_fast<M, float>(w.la, lane, w.rf.sig0, w.rf.X0, sh.U[b], &ldL, a.max_sweeps);
       }
-      if (rc == kOk) warp_refine_gevd<M>(w.rf, w.rf.X0, w.la.Z, lane);
+      if (rc == kOk) warp_refine_gevd<M>(w.rf, w.rf.X0, w.la.Z, w.la.A2, w.la.V2, w.la.V, w.la.L, lane);
     }
     if (rc == kOk) {
-      for (int e = lane; e < MM; e += 32) sh.Q[b][e / M][e % M] = w.rf.X[e / M][e % M];
+      for (int e = lane; e < MM; e += 32) {
+        const double2 qv = w.rf.X[e / M][e % M];
+        sh.Q[b][e / M][e % M] = qv;
+        split2(qv, sh.Qh[e / M][e % M], sh.Ql[e / M][e % M]);
+      }
       if (lane < M) {
         const double l = w.rf.lam[lane];
         sh.sig[b][lane] = l;
@@ -514,6 +527,10 @@ __device__ int fast_solve(Sh& sh, FastWork<GM>& w, const FastEmArgs& a, int b, i
       rc = warp_gevd_fast<M, ST2>(w.la, lane, sh.sig[b], sh.Q[b], sh.U[b], &ldL, a.max_sweeps);
     }
     if (lane == 0) sh.ldL[b] = ldL;
+    if constexpr (GM == 1) {
+      for (int e = lane; e < MM; e += 32) split2(sh.Q[b][e / M][e % M], sh.Qh[e / M][e % M], sh.Ql[e / M][e % M]);
+      __syncwarp();
+    }
   }
   if (rc != kOk && lane == 0) {
     set_status(a.status, rc);
@@ -522,21 +539,46 @@ __device__ int fast_solve(Sh& sh, FastWork<GM>& w, const FastEmArgs& a, int b, i
   return rc;
 }
 
-// Publish the next basis for the bin pass: P^H <- (P Q)^H, from the FP32 copies (FP32
-// eigensolver) or formed in FP64 and then rounded (an FP32 product of the rounded factors loses
-// accuracy in the small columns of an ill-conditioned P), and Lambda <- Sigma. After the
-// deferred basis update of the previous iteration. One warp.
+// Publish the next basis for the bin pass: P^H <- (P Q)^H and Lambda <- Sigma. FP32
+// eigensolver: from the FP32 copies. FP64 modes: P Q is needed to FP32 accuracy in every entry,
+// which an FP32 product of the rounded factors does not give for an ill-conditioned P (its small
+// columns come from cancellation), so it is a compensated dot product (Dot2) of the split pairs
+// P = P32 + P32lo and Q = Qh + Ql on the FP32 pipe (for M <= 4 the lanes of a pair split each
+// sum). After the deferred basis update of the previous iteration. One warp.
 template <int M, int GM, typename Sh>
 __device__ void fast_publish(Sh& sh, int b, float gi, int lane) {
   constexpr int MM = M * M;
-  for (int e = lane; e < MM; e += 32) {
-    const int i = e / M, m = e % M;  // (P Q)_{m i}
-    if constexpr (GM != 0) {
-      double2 s = make_double2(0.0, 0.0);
+  if constexpr (GM != 0) {
+    constexpr bool kSplit = MM <= 16;
+    constexpr int kPer = kSplit ? 1 : (MM + 31) / 32;
+    constexpr int kStride = kSplit ? 2 : 1;
+    const int h = kSplit ? (lane & 1) : 0;
 #pragma unroll
-      for (int k = 0; k < M; ++k) s = zfma(sh.P[m][k], sh.Q[b][k][i], s);
-      sh.PH[i][m] = make_float2((float)s.x * gi, -(float)s.y * gi);
-    } else {
+    for (int t = 0; t < kPer; ++t) {
+      const int e = kSplit ? (lane >> 1) : lane + 32 * t;
+      const int i = (e < MM) ? e / M : 0, m = (e < MM) ? e % M : 0;  // (P Q)_{m i}
+      CDot2 acc;
+      if (e < MM) {
+#pragma unroll
+        for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
+          const int k = kk * kStride + h;
+          if (k < M) {
+            const float2 ph = sh.P32[m][k], pl = sh.P32lo[m][k], qh = sh.Qh[k][i];
+            acc.fma2(ph, qh, sh.Ql[k][i]);
+            acc.re.c = fmaf(pl.x, qh.x, fmaf(-pl.y, qh.y, acc.re.c));
+            acc.im.c = fmaf(pl.x, qh.y, fmaf(pl.y, qh.x, acc.im.c));
+          }
+        }
+      }
+      if constexpr (kSplit) acc.shfl_merge(1);
+      if (e < MM && h == 0) {
+        const double2 v = acc.value();
+        sh.PH[i][m] = make_float2((float)v.x * gi, -(float)v.y * gi);
+      }
+    }
+  } else {
+    for (int e = lane; e < MM; e += 32) {
+      const int i = e / M, m = e % M;  // (P Q)_{m i}
       float2 s = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < M; ++k) s = cfma(sh.P32[m][k], sh.Q[b][k][i], s);
