@@ -151,13 +151,16 @@ fca_status fca_sync_status(fca_state* s, void* cuda_stream);
  * feed it (Eq. (updateStildeeff)).
  *   FCA_GEVD_FP32:    both in FP32.
  *   FCA_GEVD_FP64:    both in FP64 (the per-warp partial sums over frames stay FP32).
- *   FCA_GEVD_REFINED: the merge in FP64; the Cholesky and Jacobi solve in FP32, then Q is
- *                     refined in FP64 against the FP64 Grams until Q^H St2 Q = I and
- *                     Q^H St1 Q is diagonal to second order in the FP32 solve's residuals
- *                     (one Newton-type correction step, two after a poor start).
- * In the FP64 and refined modes the next basis P Q is formed in FP64 before it is rounded for
- * the bin pass. The bin pass is FP32 and the basis P, log-likelihood and log det S2 are kept
- * in FP64 in every mode. Batches (fca_batch_*) run the FP32 or the refined mode. */
+ *   FCA_GEVD_REFINED: the merge in FP64; an FP32 solve (Newton-type steps from the
+ *                     identity, or the FP32 Cholesky and Jacobi solve after a poor start),
+ *                     then one refinement step of Q against the FP64-merged Grams with
+ *                     compensated FP32 residuals (twice FP32's precision), and a second,
+ *                     FP64 step after a poor start: Q^H St2 Q = I and Q^H St1 Q diagonal to
+ *                     second order in the FP32 solve's residuals.
+ * In the FP64 and refined modes the next basis P Q for the bin pass is a compensated FP32
+ * product of P and Q each split into two FP32 parts, accurate to FP32 in every entry. The bin
+ * pass is FP32 and the basis P, log-likelihood and log det S2 are kept in FP64 in every mode.
+ * Batches (fca_batch_*) run the FP32 or the refined mode. */
 enum { FCA_GEVD_FP32 = 0, FCA_GEVD_FP64 = 1, FCA_GEVD_REFINED = 2 };
 #define FCA_GEVD_DEFAULT FCA_GEVD_REFINED /* of new states, batches, server requests and
                                              fca_em_fast_noalloc */

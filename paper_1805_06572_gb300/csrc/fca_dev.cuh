@@ -1298,16 +1298,46 @@ __device__ double warp_refine_step64(RefineWork<R>& w, float2 (*E)[kMaxM], int l
   return (double)emax;
 }
 
-// The first refinement step from an FP32 basis X0 (exact in FP32): warp_refine_step64 with the
-// residual products on the FP32 pipe. R = I - X0^H B X0 and S = X0^H A X0 are compensated dot
-// products (Dot2) of X0 and the split FP32 pairs of A and B, the inner products B X0 and A X0
-// kept as unrounded pairs; their error is of order 2^-48, the FP64 step's accuracy for this
-// purpose, at no FP64 multiply-add. lam in FP64, the correction E and X0 E in FP32, and
-// X = X0 + X0 E in FP64 (into w.X). Returns max_ij |E_ij|_1 (all lanes).
+// The refined basis and eigenvalues as FP32 pairs (hi + lo): X = Xh + Xl, lam = lh + ll.
+struct RefineOut {
+  float2 (*Xh)[kMaxM];
+  float2 (*Xl)[kMaxM];
+  float* lh;
+  float* ll;
+};
+
+// refine_pair in FP32, for residual entries that are small quantities needed to FP32 accuracy
+// and eigenvalues given as pairs (the gap of a close pair is formed from both parts).
+__device__ __forceinline__ float refine_pair32(float lhi, float lli, float lhj, float llj, float2 r,
+                                               float2 s, float2* eij, float2* eji) {
+  const float g = (lhj - lhi) + (llj - lli);
+  const float c1x = fmaf(lhj, r.x, s.x), c1y = fmaf(lhj, r.y, s.y);
+  const float c2x = fmaf(lhi, r.x, s.x), c2y = fmaf(lhi, r.y, s.y);
+  const float cm = fmaxf(fabsf(c1x) + fabsf(c1y), fabsf(c2x) + fabsf(c2y));
+  if (cm <= (float)kRefineSep * fabsf(g)) {
+    const float rg = __fdividef(1.f, g);
+    *eij = make_float2(c1x * rg, c1y * rg);
+    *eji = make_float2(-c2x * rg, c2y * rg);
+  } else {
+    *eij = make_float2(0.5f * r.x, 0.5f * r.y);
+    *eji = make_float2(eij->x, -eij->y);
+  }
+  return fmaxf(fabsf(eij->x) + fabsf(eij->y), fabsf(eji->x) + fabsf(eji->y));
+}
+
+// The first refinement step from an FP32 basis X0 (exact in FP32), in FP32 arithmetic only:
+// the step of warp_refine_step64 with R = I - X0^H B X0 and S = X0^H A X0 formed as
+// compensated dot products (Dot2) of X0 and the split FP32 pairs of A and B (B X0 and A X0
+// kept as unrounded pairs): an error of order 2^-48 of the terms, which for a basis near the
+// pencil's eigenbasis is 2^-48 of the result. The small quantities (R, the off-diagonal of S,
+// the couplings and E) are then needed to FP32 accuracy only; the eigenvalues
+// lam_i = s_ii (1 + r_ii + r_ii^2) and the basis X = X0 + X0 E are kept as FP32 pairs
+// (out.lh, out.ll; out.Xh = X0, out.Xl = X0 E). Returns max_ij |E_ij|_1 (all lanes).
 template <int M, int R>
-__device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM],
-                                      float2 (*T1h)[kMaxM], float2 (*T1l)[kMaxM],
-                                      float2 (*T2h)[kMaxM], float2 (*T2l)[kMaxM], int lane) {
+__device__ float warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM],
+                                     float2 (*T1h)[kMaxM], float2 (*T1l)[kMaxM],
+                                     float2 (*T2h)[kMaxM], float2 (*T2l)[kMaxM],
+                                     const RefineOut& out, int lane) {
   constexpr int MM = M * M;
   constexpr bool kSplit = MM <= 16;
   constexpr int kPer = kSplit ? 1 : (MM + 31) / 32;
@@ -1343,8 +1373,8 @@ __device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM
     }
   }
   __syncwarp();
-  // R = I - X0^H T1, S = X0^H T2; lam
-  double2 r[kPer], sv[kPer];
+  // R = I - X0^H T1, S = X0^H T2 (FP32 values); lam as pairs
+  float2 r[kPer], sv[kPer];
 #pragma unroll
   for (int t = 0; t < kPer; ++t) {
     const int e = entry(t);
@@ -1365,13 +1395,25 @@ __device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM
       q.shfl_merge(1);
       u.shfl_merge(1);
     }
-    const double2 qv = q.value();
-    r[t] = make_double2((i == j ? 1.0 : 0.0) - qv.x, -qv.y);
-    sv[t] = u.value();
-    if (e < MM && h == 0 && i == j) w.lam[i] = fma(sv[t].x, fma(r[t].x, r[t].x, r[t].x), sv[t].x);
+    if (i == j) {
+      // 1 - q_ii is exact in FP32 for q_ii near 1; s_ii as a normalised pair
+      r[t] = make_float2((1.f - q.re.s) - q.re.c, 0.f);
+      float shi, slo;
+      two_sum(u.re.s, u.re.c, shi, slo);
+      sv[t] = make_float2(shi, 0.f);
+      if (e < MM && h == 0) {
+        float lh, ll;
+        two_sum(shi, fmaf(shi, fmaf(r[t].x, r[t].x, r[t].x), slo), lh, ll);
+        out.lh[i] = lh;
+        out.ll[i] = ll;
+      }
+    } else {
+      r[t] = make_float2(-(q.re.s + q.re.c), -(q.im.s + q.im.c));
+      sv[t] = make_float2(u.re.s + u.re.c, u.im.s + u.im.c);
+    }
   }
   __syncwarp();
-  // E (FP32), as in warp_refine_step64
+  // E: the pair's upper entry writes both corrections
   float emax = 0.f;
 #pragma unroll
   for (int t = 0; t < kPer; ++t) {
@@ -1380,11 +1422,11 @@ __device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM
       const int i = e / M, j = e % M;
       float m = 0.f;
       if (i == j) {
-        E[i][i] = make_float2((float)(0.5 * r[t].x), 0.f);
-        m = fabsf(E[i][i].x);
-      } else if (i < j) {  // the pair's upper entry writes both corrections
+        E[i][i] = make_float2(0.5f * r[t].x, 0.f);
+        m = fabsf(0.5f * r[t].x);
+      } else if (i < j) {
         float2 eij, eji;
-        m = refine_pair(w.lam[i], w.lam[j], r[t], sv[t], &eij, &eji);
+        m = refine_pair32(out.lh[i], out.ll[i], out.lh[j], out.ll[j], r[t], sv[t], &eij, &eji);
         E[i][j] = eij;
         E[j][i] = eji;
       }
@@ -1397,7 +1439,7 @@ __device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM
     emax = (other > emax || other != other) ? other : emax;
   }
   __syncwarp();
-  // X = X0 + X0 E: the product in FP32, the sum in FP64
+  // X = X0 + X0 E, kept as the pair (X0, X0 E)
 #pragma unroll
   for (int t = 0; t < kPer; ++t) {
     const int e = entry(t);
@@ -1415,25 +1457,40 @@ __device__ double warp_refine_step_df(RefineWork<R>& w, const float2 (*X0)[kMaxM
       d.y += __shfl_xor_sync(0xffffffffu, d.y, 1);
     }
     if (e < MM && h == 0) {
-      const float2 x0 = X0[i][j];
-      w.X[i][j] = make_double2((double)x0.x + (double)d.x, (double)x0.y + (double)d.y);
+      out.Xh[i][j] = X0[i][j];
+      out.Xl[i][j] = d;
     }
   }
   __syncwarp();
-  return (double)emax;
+  return emax;
 }
 
-// Refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B): Newton-type steps, the first
-// with compensated FP32 residuals (warp_refine_step_df), a second in FP64
-// (warp_refine_step64) when the first correction exceeded 1e-4 (a poor start); the result is
-// X^H B X = I and X^H A X = diag(lam) to second order in the FP32 residuals. Leaves X in w.X
-// and lam in w.lam. E, T1h..T2l: FP32 workspaces. All 32 lanes; ends with __syncwarp().
+// Refinement of an FP32 generalised eigenbasis X0 of (w.A, w.B) into out: the FP32 step of
+// warp_refine_step_df, and when its correction exceeded 1e-4 (a poor start) a second,
+// FP64 step (warp_refine_step64, through w.X and w.lam). The result satisfies X^H B X = I and
+// X^H A X = diag(lam) to second order in the start's residuals. X0 must not be out.Xh or
+// out.Xl; E, T1h..T2l: FP32 workspaces. All 32 lanes; ends with __syncwarp().
 template <int M, int R>
 __device__ void warp_refine_gevd(RefineWork<R>& w, const float2 (*X0)[kMaxM], float2 (*E)[kMaxM],
                                  float2 (*T1h)[kMaxM], float2 (*T1l)[kMaxM], float2 (*T2h)[kMaxM],
-                                 float2 (*T2l)[kMaxM], int lane) {
-  const double em = warp_refine_step_df<M>(w, X0, E, T1h, T1l, T2h, T2l, lane);
-  if (em > 1e-4) warp_refine_step64<M>(w, E, lane);
+                                 float2 (*T2l)[kMaxM], const RefineOut& out, int lane) {
+  constexpr int MM = M * M;
+  const float em = warp_refine_step_df<M>(w, X0, E, T1h, T1l, T2h, T2l, out, lane);
+  if (em <= 1e-4f) return;  // (NaN goes on, and stays NaN)
+  for (int e = lane; e < MM; e += 32) {
+    const float2 hi = out.Xh[e / M][e % M], lo = out.Xl[e / M][e % M];
+    w.X[e / M][e % M] = make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+  }
+  __syncwarp();
+  warp_refine_step64<M>(w, E, lane);
+  for (int e = lane; e < MM; e += 32) split2(w.X[e / M][e % M], out.Xh[e / M][e % M], out.Xl[e / M][e % M]);
+  if (lane < M) {
+    const double l = w.lam[lane];
+    const float lh = (float)l;
+    out.lh[lane] = lh;
+    out.ll[lane] = (float)(l - (double)lh);
+  }
+  __syncwarp();
 }
 
 // log det B of a Hermitian positive definite B near the identity (FP64, shared memory), by an

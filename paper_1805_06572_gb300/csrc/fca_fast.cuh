@@ -15,11 +15,12 @@
 //     merge in a fixed order (bitwise reproducible): the Gram entries in the precision G of
 //     the eigensolver they feed (FP32, or FP64), the log-likelihood sums compensated into
 //     FP64;
-//   warp 0: generalised eigenproblem of (St1, St2) (Algorithm 1, step 8) in precision G and
-//     the next basis P^H for the bin pass; meanwhile warp 1 does the previous iteration's FP64
+//   one warp (the role rotates over the CTA's warps with the iteration): the generalised
+//     eigenproblem of (St1, St2) (Algorithm 1, step 8) in precision G and the next basis P^H
+//     for the bin pass; meanwhile the next warp does the previous iteration's FP64
 //     bookkeeping: P <- P Q (Eq. (updatePeff)), Lambda <- Sigma (Eq. (updateLambdaeff)),
-//     log det S2 <- log det S2 - log|det Q|^2 (S2 = P^-H P^-1 for the basis in use), and the
-//     previous iteration's log-likelihood.
+//     and a third (or the same) warp log det S2 <- log det S2 - log|det Q|^2
+//     (S2 = P^-H P^-1 for the basis in use) and the previous iteration's log-likelihood.
 // The log-likelihood of iteration l uses log det Rx = sum_i log d_i + log det S2 and
 // y^H Rx^-1 y = sum_i |yt_i|^2 / d_i, which follow from Rx = P^-H (v1 Lam + v2 I) P^-1.
 // The mixture and v stay in shared memory across iterations when they fit.
@@ -34,7 +35,9 @@ namespace fca {
 // Precision modes of the per-bin generalised eigenproblem (FCA_GEVD_* in fca.h):
 //   0  FP32 merge of the Gram partials, FP32 Cholesky + Jacobi, FP32 Q;
 //   1  FP64 merge, FP64 Cholesky + Jacobi, FP64 Q;
-//   2  FP64 merge, FP32 Newton-type iteration (or Cholesky + Jacobi), FP64 refinement of Q.
+//   2  FP64 merge, FP32 Newton-type iteration (or Cholesky + Jacobi), one refinement step of
+//      Q with compensated FP32 residuals (a second, FP64 step after a poor start); Q and Sigma
+//      as FP32 pairs, made FP64 by the deferred bookkeeping.
 template <int GM> struct GevdTypes;
 template <> struct GevdTypes<0> { using Merge = float; using Solve = float; using Out = float; };
 template <> struct GevdTypes<1> { using Merge = double; using Solve = double; using Out = double; };
@@ -53,8 +56,7 @@ struct FastBin {
   double2 P[M][kMaxM];      // basis P (FP64); M x M matrices with leading dimension kMaxM
   float2 P32[M][kMaxM];     // P rounded to FP32
   float2 P32lo[M][kMaxM];   // P - P32 rounded to FP32 (FP64 modes: the next basis is
-  float2 Qh[M][kMaxM];      //   published from these pairs and Q = Qh + Ql)
-  float2 Ql[M][kMaxM];
+                            //   published from the pairs of P and Q)
   float2 PH[M][M];              // FP32 P^H (times the decode scale) used by the bin pass
   float lam[M], ilam[M];
   double lam64[kMaxM];
@@ -63,6 +65,11 @@ struct FastBin {
   Cx<OutT> Q[2][M][kMaxM];
   Cx<SolveT> U[2][M][kMaxM];
   OutT sig[2][kMaxM];
+  // FP64 modes: Q = Qh + Ql and Sigma = sigh + sigl as FP32 pairs (the refined eigensolver's
+  // own result, from which the deferred bookkeeping forms Q and Sigma in FP64)
+  float2 Qh[2][M][kMaxM];
+  float2 Ql[2][M][kMaxM];
+  float sigh[2][kMaxM], sigl[2][kMaxM];
   OutT ldL[2];       // modes 0, 1: 2 sum log(1/L_ii), log|det Q|^2 = ldL + log|det U|^2;
                      // mode 2: log|det Q|^2 itself (= -log det St2)
   double llt[2][2];  // sum log d, sum p/d of the iteration
@@ -162,10 +169,18 @@ __device__ __forceinline__ void merge_store(C (*D)[kMaxM], int i, int k, int par
 // Deferred FP64 bookkeeping of iteration `it`, in two parts that may run on two warps at once.
 // Basis part: P <- P Q (Eq. (updatePeff)) and its FP32 copy, Lambda <- Sigma
 // (Eq. (updateLambdaeff)), and at it = L-2 the basis of iteration L-1.
-template <int M, typename Sh>
+template <int M, int GM, typename Sh>
 __device__ void fast_deferred_basis(Sh& sh, const FastEmArgs& a, int f, int it, int lane) {
   constexpr int MM = M * M;
   const int b = it & 1;
+  if constexpr (GM == 2) {  // Q and Sigma in FP64 from the eigensolver's pairs
+    for (int e = lane; e < MM; e += 32) {
+      const float2 hi = sh.Qh[b][e / M][e % M], lo = sh.Ql[b][e / M][e % M];
+      sh.Q[b][e / M][e % M] = make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+    }
+    if (lane < M) sh.sig[b][lane] = (double)sh.sigh[b][lane] + (double)sh.sigl[b][lane];
+    __syncwarp();
+  }
   if constexpr (2 * MM <= 32) {
     warp_update_basis_q2<M>(sh.P, sh.Q[b], lane);
   } else {
@@ -483,20 +498,23 @@ __device__ int fast_solve(Sh& sh, FastWork<M, GM>& w, const FastEmArgs& a, int b
   if constexpr (GM == 2) {
     // Newton-type iteration from the identity (the basis P already diagonalises the
     // previous iteration's parameters, so the new Grams are nearly diagonal in it): FP32
-    // steps, then the FP64 refinement against the FP64 Grams. A poor start (a first
-    // correction above 0.1, or steps that do not converge quadratically) takes the FP32
-    // Cholesky + Jacobi solver instead, whose basis the FP64 steps then refine.
+    // steps until the correction is below 1e-3 (the basis then has residuals of order 1e-6,
+    // which the compensated refinement step squares), then the refinement against the
+    // FP64-merged Grams. A poor start (a first correction above 0.1, or steps that do not
+    // converge quadratically) takes the FP32 Cholesky + Jacobi solver instead, whose basis
+    // is then refined the same way.
     rc = kOk;
     float em = warp_newton_step<M, float>(w.la.A, w.la.L, w.la.V, w.la.Z, w.la.A2, w.rf.lam32, true, lane);
     bool newton = em <= 0.1f;
-    for (int k = 0; newton && em > 1e-5f && k < 4; ++k) {
+    for (int k = 0; newton && em > 1e-3f && k < 4; ++k) {
       const float en = warp_newton_step<M, float>(w.la.A, w.la.L, w.la.V, w.la.Z, w.la.A2, w.rf.lam32,
                                                   false, lane);
       newton = en <= 0.5f * em;
       em = en;
     }
+    const RefineOut out{sh.Qh[b], sh.Ql[b], sh.sigh[b], sh.sigl[b]};
     if (newton) {
-      warp_refine_gevd<M>(w.rf, w.la.V, w.la.Z, w.la.A2, w.la.V2, w.la.A, w.la.L, lane);  // A, L free now
+      warp_refine_gevd<M>(w.rf, w.la.V, w.la.Z, w.la.A2, w.la.V2, w.la.A, w.la.L, out, lane);  // A, L free now
     } else {
       if constexpr (M <= 4) {
         rc = warp_gevd_reg<M, float>(w.la.A, w.la.L, w.rf.sig0, w.rf.X0, sh.U[b], &ldL,
@@ -504,18 +522,12 @@ __device__ int fast_solve(Sh& sh, FastWork<M, GM>& w, const FastEmArgs& a, int b
       } else {
         rc = warp_gevd_fast<M, float>(w.la, lane, w.rf.sig0, w.rf.X0, sh.U[b], &ldL, a.max_sweeps);
       }
-      if (rc == kOk) warp_refine_gevd<M>(w.rf, w.rf.X0, w.la.Z, w.la.A2, w.la.V2, w.la.V, w.la.L, lane);
+      if (rc == kOk) warp_refine_gevd<M>(w.rf, w.rf.X0, w.la.Z, w.la.A2, w.la.V2, w.la.V, w.la.L, out, lane);
     }
     if (rc == kOk) {
-      for (int e = lane; e < MM; e += 32) {
-        const double2 qv = w.rf.X[e / M][e % M];
-        sh.Q[b][e / M][e % M] = qv;
-        split2(qv, sh.Qh[e / M][e % M], sh.Ql[e / M][e % M]);
-      }
       if (lane < M) {
-        const double l = w.rf.lam[lane];
-        sh.sig[b][lane] = l;
-        if (!(l > 0.0) || !(l < 1e300)) rc = kErrNotPD;
+        const float l = sh.sigh[b][lane];
+        if (!(l > 0.f) || !(l < Prec<float>::kHuge)) rc = kErrNotPD;
       }
       rc = __reduce_max_sync(0xffffffffu, rc);  // warp-uniform
     }
@@ -528,7 +540,7 @@ __device__ int fast_solve(Sh& sh, FastWork<M, GM>& w, const FastEmArgs& a, int b
     }
     if (lane == 0) sh.ldL[b] = ldL;
     if constexpr (GM == 1) {
-      for (int e = lane; e < MM; e += 32) split2(sh.Q[b][e / M][e % M], sh.Qh[e / M][e % M], sh.Ql[e / M][e % M]);
+      for (int e = lane; e < MM; e += 32) split2(sh.Q[b][e / M][e % M], sh.Qh[b][e / M][e % M], sh.Ql[b][e / M][e % M]);
       __syncwarp();
     }
   }
@@ -563,8 +575,8 @@ __device__ void fast_publish(Sh& sh, int b, float gi, int lane) {
         for (int kk = 0; kk < (M + kStride - 1) / kStride; ++kk) {
           const int k = kk * kStride + h;
           if (k < M) {
-            const float2 ph = sh.P32[m][k], pl = sh.P32lo[m][k], qh = sh.Qh[k][i];
-            acc.fma2(ph, qh, sh.Ql[k][i]);
+            const float2 ph = sh.P32[m][k], pl = sh.P32lo[m][k], qh = sh.Qh[b][k][i];
+            acc.fma2(ph, qh, sh.Ql[b][k][i]);
             acc.re.c = fmaf(pl.x, qh.x, fmaf(-pl.y, qh.y, acc.re.c));
             acc.im.c = fmaf(pl.x, qh.y, fmaf(pl.y, qh.x, acc.im.c));
           }
@@ -586,7 +598,7 @@ __device__ void fast_publish(Sh& sh, int b, float gi, int lane) {
     }
   }
   if (lane < M) {
-    const float sg = (float)sh.sig[b][lane];
+    const float sg = (GM == 2) ? sh.sigh[b][lane] + sh.sigl[b][lane] : (float)sh.sig[b][lane];
     sh.lam[lane] = sg;
     sh.ilam[lane] = 1.f / sg;
   }
@@ -692,7 +704,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
     if (warp == ws) {
       fast_solve<M, GM>(sh, sh.w, a, b, lane);
     } else if (warp == wb && it > 0) {
-      fast_deferred_basis<M>(sh, a, f, it - 1, lane);
+      fast_deferred_basis<M, GM>(sh, a, f, it - 1, lane);
       if constexpr (NW < 3) fast_deferred_ll<M, GM>(sh, a, f, N, it - 1, lane);
     } else if (NW >= 3 && warp == wl) {
       fast_logdet<M, GM>(sh, sh.w, it, lane);
@@ -706,7 +718,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(M, NT)) fast_em_kernel(con
   }
   if (done > 0 && done == a.iters) {
     if (warp == 1) {
-      fast_deferred_basis<M>(sh, a, f, done - 1, lane);
+      fast_deferred_basis<M, GM>(sh, a, f, done - 1, lane);
       if constexpr (NW < 3) fast_deferred_ll<M, GM>(sh, a, f, N, done - 1, lane);
     } else if (NW >= 3 && warp == 2) {
       fast_deferred_ll<M, GM>(sh, a, f, N, done - 1, lane);

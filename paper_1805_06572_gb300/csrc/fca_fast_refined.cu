@@ -1,5 +1,5 @@
-// The FastFCA EM kernel for one mixture with the FP64 Gram merge, the FP32 Cholesky and Jacobi
-// eigensolver and the FP64 refinement of its basis (128 threads per CTA, both storages). A
+// The FastFCA EM kernel for one mixture with the FP64 Gram merge, the FP32 eigensolver and the
+// compensated refinement of its basis (128 threads per CTA, both storages). A
 // separate translation unit so that the library's objects compile in parallel.
 #include "fca_fast.cuh"
 
