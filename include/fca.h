@@ -69,10 +69,27 @@ enum { FCA_SEP_ALG1 = 0, FCA_SEP_FINAL_PARAMS = 1 };
  *   storage = FCA_STORE_F16_SCALED:  y is FP16 pairs [F][N][M][2] holding g_f * y(n,f), and
  *                                    y_scale[f] = g_f > 0 (float [F]); the EM runs on the
  *                                    decoded mixture y16 / g_f.
+ *                                    With y_scale = NULL (device location only), y is
+ *                                    complex64 [F][N][M] and the library encodes it:
+ *                                    g_f = (mean_{n,m} |y_m(n,f)|^2)^(-1/2) (FP64 sum, rounded
+ *                                    to float; 1 for a silent bin) and g_f y(n,f) rounded
+ *                                    to FP16 (round to nearest even, from the exact FP64
+ *                                    product).
  *   v0:  double [2][F][N], initial v_j^(0)(n,f) > 0 (clamped to the positivity floor).
  *   S0:  complex128 [2][F][M][M], initial S_j^(0)(f), Hermitian positive definite.
+ *   v0 = S0 = NULL: the seeded initial values, built on the device from `seed` and the mixture
+ *        (as the EM sees it: decoded when stored as FP16):
+ *          S_j^(0)(f) = b_j(f) b_j(f)^H + I, b_j(f) ~ CN(0, I_M),
+ *          v_j^(0)(n,f) = max(|y(n,f)|^2, eps_f) / (2 tr S_j^(0)(f)),
+ *          eps_f = 1e-12 mean_n |y(n,f)|^2,
+ *        entry m of b_j(f) being draw t = f M + m of source j: the Philox4x64-10 block of
+ *        counter (t, 0, 0, 0) under the key (seed, 1000 + j) (Salmon et al., SC 2011), whose
+ *        words w0, w1 give u_k = (floor(w_k / 2^11) + 1/2) 2^-53 and
+ *        b = sqrt(-ln u0) (cos 2 pi u1 + i sin 2 pi u1). One of v0, S0 without the other is
+ *        an argument error.
  *   location: FCA_MEM_DEVICE or FCA_MEM_HOST, for all of y, y_scale, v0 and S0. Host
  *   buffers are copied with cudaMemcpyAsync; pinned host memory makes that asynchronous.
+ *   seed: read only when v0 = S0 = NULL.
  */
 typedef struct {
   int32_t M, F, N;
@@ -82,6 +99,7 @@ typedef struct {
   const float* y_scale;
   const double* v0;
   const double* S0;
+  uint64_t seed;
 } fca_problem;
 
 /* Allocate a state for the shapes in *p and load it (as fca_load). On success *out owns the

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfca.so")
 SOURCES = ["fca_api.cu", "fca_fast.cu", "fca_fast64.cu", "fca_fast_refined.cu", "fca_fast_tuned.cu", "fca_fast_tuned_refined.cu", "fca_conv.cu", "fca_aux.cu",
-           "fca_noalloc.cu", "fca_batch.cu", "fca_server.cu", "fca_stft.cu", "fca_peak.cu"]
+           "fca_noalloc.cu", "fca_batch.cu", "fca_server.cu", "fca_stft.cu", "fca_peak.cu", "fca_init.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

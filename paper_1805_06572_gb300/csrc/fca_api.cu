@@ -95,8 +95,9 @@ bool problem_ok(const fca_problem* p) {
   if ((int64_t)p->F * p->N * p->M >= ((int64_t)1 << 31)) return false;
   if (p->storage != FCA_STORE_C64 && p->storage != FCA_STORE_F16_SCALED) return false;
   if (p->location != FCA_MEM_DEVICE && p->location != FCA_MEM_HOST) return false;
-  if (!p->y || !p->v0 || !p->S0) return false;
-  if (p->storage == FCA_STORE_F16_SCALED && !p->y_scale) return false;
+  if (!p->y || (!p->v0) != (!p->S0)) return false;
+  // FP16 storage without a scale: a complex64 mixture on the device, encoded by the library
+  if (p->storage == FCA_STORE_F16_SCALED && !p->y_scale && p->location != FCA_MEM_DEVICE) return false;
   return true;
 }
 
@@ -178,22 +179,27 @@ fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
   if (!s || !problem_ok(p)) return FCA_ERR_ARG;
   if (p->M != s->M || p->F != s->F || p->N > s->N_cap || p->storage != s->storage) return FCA_ERR_ARG;
   DeviceGuard guard(s->device);
+  const bool seeded = !p->v0;  // with S0 == NULL (problem_ok)
+  const bool encode = p->storage == FCA_STORE_F16_SCALED && !p->y_scale;
   if (p->location == FCA_MEM_DEVICE) {
-    if (!device_pointer(p->y, s->device) || !device_pointer(p->v0, s->device) ||
-        !device_pointer(p->S0, s->device) ||
-        (p->storage == FCA_STORE_F16_SCALED && !device_pointer(p->y_scale, s->device)))
+    if (!device_pointer(p->y, s->device) ||
+        (!seeded && (!device_pointer(p->v0, s->device) || !device_pointer(p->S0, s->device))) ||
+        (p->storage == FCA_STORE_F16_SCALED && !encode && !device_pointer(p->y_scale, s->device)))
       return FCA_ERR_ARG;
+    if (encode && !aligned(p->y, 8)) return FCA_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
   s->N = p->N;
   s->FN = (size_t)s->F * s->N;
   const size_t ybytes = s->FN * s->M * (s->storage ? 4 : 8);
   // Device inputs: the prepare pass copies y and S0 into the state as it reads them. Host
-  // inputs: copied up first, then read in place.
+  // inputs: copied up first, then read in place. A mixture the library encodes to FP16 is
+  // written into the state by the encoding pass; seeded initial values are written into the
+  // state's S and the v0 staging buffer.
   // (Element-misaligned device inputs take the copy route too.)
   const bool on_dev = p->location == FCA_MEM_DEVICE;
-  const bool y_direct = on_dev && aligned(p->y, s->storage ? 4 : 8);
-  const bool S_direct = on_dev && aligned(p->S0, 16);
+  const bool y_direct = on_dev && !encode && aligned(p->y, s->storage ? 4 : 8);
+  const bool S_direct = on_dev && !seeded && aligned(p->S0, 16);
   PrepareExtra ex;
   std::memset(&ex, 0, sizeof(ex));
   ex.max_sweeps = s->max_sweeps;
@@ -201,24 +207,31 @@ fca_status fca_load(fca_state* s, const fca_problem* p, void* stream) {
   ex.P = s->P;
   ex.lam = s->lam;
   ex.logdetS2 = s->logdetS2;
-  if (y_direct) {
+  if (encode) {
+    FCA_CHECK_CUDA(counted(launch_encode_f16(s->F, s->N * s->M, p->y, s->y, s->g, st)));
+  } else if (y_direct) {
     ex.y_copy = s->y;
   } else {
     FCA_CHECK_CUDA(cudaMemcpyAsync(s->y, p->y, ybytes, cudaMemcpyDefault, st));
   }
-  if (S_direct) {
+  if (s->storage == FCA_STORE_F16_SCALED) {
+    if (!encode) FCA_CHECK_CUDA(cudaMemcpyAsync(s->g, p->y_scale, s->F * sizeof(float), cudaMemcpyDefault, st));
+    FCA_CHECK_CUDA(counted(launch_invert_scale(s->F, s->g, s->ginv, st)));
+  }
+  if (seeded) {
+    if (!s->v0_stage) FCA_CHECK_CUDA(dalloc(&s->v0_stage, 2 * (size_t)s->F * s->N_cap));
+    FCA_CHECK_CUDA(counted(launch_seeded_init(s->M, s->storage, s->F, s->N, y_direct ? p->y : s->y, s->g,
+                                              (unsigned long long)p->seed, s->S, s->v0_stage, st)));
+    ex.S = s->S;
+  } else if (S_direct) {
     ex.S = static_cast<const double2*>(static_cast<const void*>(p->S0));
     ex.S_copy = s->S;
   } else {
     FCA_CHECK_CUDA(cudaMemcpyAsync(s->S, p->S0, 2 * s->F * s->MM * sizeof(double2), cudaMemcpyDefault, st));
     ex.S = s->S;
   }
-  if (s->storage == FCA_STORE_F16_SCALED) {
-    FCA_CHECK_CUDA(cudaMemcpyAsync(s->g, p->y_scale, s->F * sizeof(float), cudaMemcpyDefault, st));
-    FCA_CHECK_CUDA(counted(launch_invert_scale(s->F, s->g, s->ginv, st)));
-  }
-  const double* v0 = p->v0;
-  if (!on_dev || !aligned(p->v0, 8)) {
+  const double* v0 = seeded ? s->v0_stage : p->v0;
+  if (!seeded && (!on_dev || !aligned(p->v0, 8))) {
     if (!s->v0_stage) FCA_CHECK_CUDA(dalloc(&s->v0_stage, 2 * (size_t)s->F * s->N_cap));
     FCA_CHECK_CUDA(cudaMemcpyAsync(s->v0_stage, p->v0, 2 * s->FN * sizeof(double), cudaMemcpyDefault, st));
     v0 = s->v0_stage;

@@ -158,6 +158,12 @@ cudaError_t launch_ll_ranges(int nmix, int iters, int F, const double* llf, cons
 cudaError_t launch_ll_reduce(int F, int iters, const double* llf, double* ll, cudaStream_t st);
 // ginv[f] = 1 / g[f].
 cudaError_t launch_invert_scale(int F, const float* g, float* ginv, cudaStream_t st);
+// The seeded initial values of one mixture [F][N][M] (storage 0: complex64, 1: FP16 pairs
+// decoded by 1/g[f]): S0 into S [2][F][M][M], v0 into v0 [2][F][N] (fca_problem, fca.h).
+cudaError_t launch_seeded_init(int M, int storage, int F, int N, const void* y, const float* g,
+                               unsigned long long seed, double2* S, double* v0, cudaStream_t st);
+// FP16 storage of a complex64 mixture, NM values per bin: g[f] and the FP16 pairs into y16.
+cudaError_t launch_encode_f16(int F, int NM, const void* y, void* y16, float* g, cudaStream_t st);
 
 // Count n kernel launches in the process-wide counter behind fca_kernel_launches().
 void note_launches(int n);

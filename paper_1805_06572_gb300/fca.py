@@ -46,7 +46,7 @@ class fca_problem(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("F", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("location", ctypes.c_int32),
                 ("y", ctypes.c_void_p), ("y_scale", ctypes.c_void_p),
-                ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p)]
+                ("v0", ctypes.c_void_p), ("S0", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
 
 
 class fca_batch_problem(ctypes.Structure):
@@ -183,27 +183,36 @@ def _check(rc: int, where: str):
         raise FCAError(rc, where)
 
 
-def _problem(y, v0, S0, y_scale):
+def _problem(y, v0, S0, y_scale, seed=0, encode_f16=False):
     if y.dtype == torch.complex64:
         F, N, M = y.shape
-        storage = FCA_STORE_C64
+        storage = FCA_STORE_F16_SCALED if encode_f16 else FCA_STORE_C64
+        if encode_f16 and (y_scale is not None or not y.is_cuda):
+            raise ValueError("encode_f16 takes a complex64 mixture on the device and no y_scale")
     elif y.dtype == torch.float16:
         F, N, M, two = y.shape
         assert two == 2
         storage = FCA_STORE_F16_SCALED
+        if y_scale is None:
+            raise ValueError("a float16 mixture needs its y_scale")
     else:
         raise TypeError("y must be complex64 [F,N,M] or float16 [F,N,M,2]")
-    for t in (y, v0, S0) + ((y_scale,) if y_scale is not None else ()):
+    if (v0 is None) != (S0 is None):
+        raise ValueError("give both v0 and S0, or neither (seeded initial values)")
+    for t in (y, v0, S0, y_scale):
+        if t is None:
+            continue
         if not t.is_contiguous():
             raise ValueError("inputs must be contiguous")
         if t.is_cuda != y.is_cuda:
             raise ValueError("y, y_scale, v0 and S0 must all be on the device or all on the host")
-    if v0.dtype != torch.float64 or S0.dtype != torch.complex128:
+    if v0 is not None and (v0.dtype != torch.float64 or S0.dtype != torch.complex128):
         raise TypeError("v0 must be float64 [2,F,N], S0 complex128 [2,F,M,M]")
     p = fca_problem(M=M, F=F, N=N, storage=storage,
                     location=FCA_MEM_DEVICE if y.is_cuda else FCA_MEM_HOST,
                     y=y.data_ptr(), y_scale=None if y_scale is None else y_scale.data_ptr(),
-                    v0=v0.data_ptr(), S0=S0.data_ptr())
+                    v0=None if v0 is None else v0.data_ptr(),
+                    S0=None if S0 is None else S0.data_ptr(), seed=int(seed) & (2**64 - 1))
     return p
 
 
@@ -219,15 +228,18 @@ class State:
             self.handle = None
 
 
-def fca_init(y, v0, S0, y_scale=None, stream=None) -> State:
-    p = _problem(y, v0, S0, y_scale)
+def fca_init(y, v0=None, S0=None, y_scale=None, stream=None, seed=0, encode_f16=False) -> State:
+    """v0 = S0 = None: the library's seeded initial values from `seed` (fca_problem in fca.h).
+    encode_f16: store the complex64 device mixture y as FP16 with a per-frequency scale, encoded
+    by the library."""
+    p = _problem(y, v0, S0, y_scale, seed, encode_f16)
     out = ctypes.c_void_p()
     _check(lib.fca_init(ctypes.byref(p), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "fca_init")
     return State(out.value, p.M, p.F, p.N, p.storage)
 
 
-def fca_load(state: State, y, v0, S0, y_scale=None, stream=None):
-    p = _problem(y, v0, S0, y_scale)
+def fca_load(state: State, y, v0=None, S0=None, y_scale=None, stream=None, seed=0, encode_f16=False):
+    p = _problem(y, v0, S0, y_scale, seed, encode_f16)
     _check(lib.fca_load(ctypes.c_void_p(state.handle), ctypes.byref(p), ctypes.c_void_p(_stream(stream))),
            "fca_load")
 

@@ -19,9 +19,14 @@ the spatial covariances from time-frequency masks). Two recipes:
     m_1(n,f) = [|x_1(n,f)|^2 > |x_2(n,f)|^2], m_2 = 1 - m_1, taken from the generator's source
     images, gives S_j^(0)(f) = mean over {n : m_j = 1} of M y y^H / |y|^2, plus 0.01 I
     (I when the mask is empty), and v_j^(0)(n,f) = max(|y|^2, eps_f) (0.1 + 0.8 m_j) / tr S_j^(0);
-  * "random": b_j(f) ~ CN(0, I_M) from PCG64(seed + 1000 + j), S_j^(0)(f) = b_j b_j^H + I and
-    v_j^(0)(n, f) = max(|y(n,f)|^2, eps_f) / (2 tr S_j^(0)(f)).
-eps_f = 1e-12 mean_n |y(n,f)|^2.
+  * "random": S_j^(0)(f) = b_j b_j^H + I and v_j^(0)(n, f) = max(|y(n,f)|^2, eps_f) /
+    (2 tr S_j^(0)(f)), with b_j(f) ~ CN(0, I_M) from a counter-based generator, so that the
+    same values can be drawn independently anywhere (the CUDA library draws them on the device
+    for a problem given without initial values): entry m of b_j(f) is draw t = f M + m of
+    source j, taken from the Philox4x64-10 block of counter (t, 0, 0, 0) under the key
+    (seed, 1000 + j) (numpy.random.Philox), whose words w0, w1 give
+    u_k = (floor(w_k / 2^11) + 1/2) 2^-53 and b = sqrt(-ln u0) (cos 2 pi u1 + i sin 2 pi u1).
+eps_f = 1e-12 mean_n |y(n,f)|^2, |y|^2 = sum_m (re^2 + im^2).
 """
 from __future__ import annotations
 
@@ -89,14 +94,27 @@ def init_params(y: np.ndarray, seed: int, x: np.ndarray | None = None, recipe: s
     yd = y.astype(np.complex128)
     S0 = np.empty((2, F, M, M), np.complex128)
     for j in range(2):
-        rng = np.random.Generator(np.random.PCG64(seed + 1000 + j))
-        b = _cn(rng, (F, M))
+        b = philox_cn(seed, j, F * M).reshape(F, M)
         S0[j] = np.einsum("fi,fj->fij", b, b.conj()) + np.eye(M)
-    pw = np.sum(np.abs(yd) ** 2, axis=2)                                # [F][N]
+    pw = np.sum(yd.real ** 2 + yd.imag ** 2, axis=2)                    # [F][N]
     eps = 1e-12 * pw.mean(axis=1, keepdims=True)
     tr = np.real(np.einsum("kfii->kf", S0))                             # [2][F]
     v0 = np.maximum(pw, eps)[None] / (2.0 * tr[:, :, None])
     return v0, S0
+
+
+def philox_cn(seed: int, j: int, count: int) -> np.ndarray:
+    """Draws 0..count-1 of source j of the "random" recipe (module docstring): CN(0, 1) values
+    from the Philox4x64-10 blocks of counters 0..count-1 under the key (seed, 1000 + j)."""
+    # numpy's Philox advances its 256-bit counter before each block: start from all ones.
+    bg = np.random.Philox(counter=np.full(4, 2**64 - 1, dtype=np.uint64),
+                          key=np.array([seed % 2**64, 1000 + j], dtype=np.uint64))
+    w = bg.random_raw(4 * count).reshape(count, 4)
+    u0 = ((w[:, 0] >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    u1 = ((w[:, 1] >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    r = np.sqrt(-np.log(u0))
+    th = 2 * np.pi * u1
+    return r * np.cos(th) + 1j * (r * np.sin(th))
 
 
 def _mask_init(y: np.ndarray, x: np.ndarray):
@@ -122,13 +140,15 @@ def _mask_init(y: np.ndarray, x: np.ndarray):
 
 
 def quantize_f16(y: np.ndarray):
-    """FP16 storage of y with a per-frequency power scale g_f = (mean_n |y|^2 / M)^(-1/2).
+    """FP16 storage of y with a per-frequency power scale g_f = (mean_n |y|^2 / M)^(-1/2)
+    (FP64 mean of re^2 + im^2 over the bin's N M values, 1 / sqrt in FP64, rounded to float32;
+    g_f y formed exactly in FP64 and rounded to float16, nearest even).
 
     Returns (y16 float16 [F][N][M][2] interleaved re/im of g_f y, g float32 [F]) and the
     dequantised complex128 mixture y16 / g_f that the EM actually sees."""
     F, N, M = y.shape
     yd = y.astype(np.complex128)
-    p = np.mean(np.abs(yd) ** 2, axis=(1, 2))
+    p = np.mean(yd.real ** 2 + yd.imag ** 2, axis=(1, 2))
     g = np.where(p > 0, 1.0 / np.sqrt(np.where(p > 0, p, 1.0)), 1.0).astype(np.float32)
     s = yd * g.astype(np.float64)[:, None, None]
     y16 = np.stack([s.real, s.imag], axis=-1).astype(np.float16)
