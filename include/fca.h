@@ -184,6 +184,21 @@ enum { FCA_GEVD_FP32 = 0, FCA_GEVD_FP64 = 1, FCA_GEVD_REFINED = 2 };
                                              fca_em_fast_noalloc */
 #define FCA_MAX_SWEEPS_LIMIT 1000
 
+/* How the conventional EM kernel (fca_em_conventional; Sec. 2, Eqs. (MMSE)-(Supdate)) maps its
+ * per-point matrix work onto threads; the arithmetic and results are the same up to rounding.
+ *   FCA_CONV_THREAD: one thread per time-frequency point, every per-point matrix (the Cholesky
+ *                    factor of Rx, L^-1 S_j, C) in its registers; for M >= 6 they exceed the
+ *                    register file and spill to local memory.
+ *   FCA_CONV_GROUP:  eight lanes per point (four for M <= 4), each owning one row or column of
+ *                    those matrices; no spills at any M.
+ *   FCA_CONV_AUTO:   the faster layout as measured on GB300, FCA_CONV_THREAD at every M
+ *                    (the default). */
+enum { FCA_CONV_AUTO = 0, FCA_CONV_THREAD = 1, FCA_CONV_GROUP = 2 };
+
+/* Choose the conventional kernel's layout for this state's later fca_em_conventional calls.
+ * Host only; returns at once. FCA_ERR_ARG for an unknown layout. */
+fca_status fca_set_conv_layout(fca_state* s, int32_t layout);
+
 /* Set the eigensolver precision (FCA_GEVD_FP32, _FP64 or _REFINED) and its cap on Jacobi sweeps
  * per eigenproblem, 0 <= max_sweeps <= FCA_MAX_SWEEPS_LIMIT (a new state has the library
  * default precision and a cap of 30). A solve that needs more sweeps stops, records

@@ -73,6 +73,7 @@ struct fca_state {
   int failed;
   int gevd_mode;   // FastFCA eigensolver and Gram merge precision (FCA_GEVD_*)
   int max_sweeps;  // Jacobi sweep cap
+  int conv_layout; // FCA_CONV_*
 };
 
 namespace {
@@ -456,6 +457,7 @@ fca_status fca_em_conventional(fca_state* s, int32_t iters, double* loglik_dev, 
   a.S_prev = s->S_prev;
   a.llf = s->llf;
   a.status = s->status;
+  a.layout = s->conv_layout;
   FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[0], st));
   FCA_CHECK_CUDA(counted(launch_conv_em(s->M, s->storage, a, st)));
   FCA_CHECK_CUDA(cudaEventRecord(s->ev_em[1], st));
@@ -586,6 +588,13 @@ fca_status fca_set_eigensolver(fca_state* s, int32_t precision, int32_t max_swee
   // A state just loaded holds S0 and the eigenproblem of S0 solved with the old settings: the
   // next fca_em_fast solves it again with these.
   if (s->form == kFormSP) s->form = kFormS;
+  return FCA_OK;
+}
+
+fca_status fca_set_conv_layout(fca_state* s, int32_t layout) {
+  if (!s || (layout != FCA_CONV_AUTO && layout != FCA_CONV_THREAD && layout != FCA_CONV_GROUP))
+    return FCA_ERR_ARG;
+  s->conv_layout = layout;
   return FCA_OK;
 }
 

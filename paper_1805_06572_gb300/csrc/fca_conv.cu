@@ -13,6 +13,14 @@
 // then the CTA merges the Gram partial sums (FP32 warp transpose-reduction, FP64 across
 // warps) and sets S_j' = Gram_j / N in FP64. The Cholesky factors K_j of S_j for the next v
 // update are formed once per frequency per iteration by warp 0 (FP64 factorisation).
+// For M >= 6 the per-point matrices do not fit one thread's registers and spill. The other
+// layout (FCA_CONV_GROUP) has a group of G = 8 lanes (4 for M <= 4) share each point
+// (conv_group_point): lane r owns row r of Rx and L, column r of L^-1 and of L^-1 S_j, row r
+// of C and of the Gram partial sums, and the group exchanges values by shuffles and per-group
+// shared tiles; it spills at no M, but runs slower (conv_grouped).
+#include <type_traits>
+
+#include "fca.h"
 #include "fca_dev.cuh"
 #include "fca_internal.h"
 
@@ -23,11 +31,11 @@ struct ConvShared {
   static constexpr int V = 2 * M * M + 2;
   float red[NW][V];
   double tot[V];
-  double2 S[2][kMaxM][kMaxM];
+  double2 S[2][M][kMaxM];
   float2 S32[2][M][M];
   float2 K32[2][M][M];  // S32_j = K_j K_j^H
   int fail;
-  WarpLAT<double> la;
+  WarpLAT<double, M> la;
 };
 
 __host__ __device__ constexpr int cpair_index(int M, int i, int k) {  // i < k
@@ -37,8 +45,8 @@ __host__ __device__ constexpr int cpair_index(int M, int i, int k) {  // i < k
 // The FP32 copy S32 of the FP64 S_j used by the bin pass, and the Cholesky factor K of S32
 // itself (S32 = K K^H; factorised in FP64 from the exact FP32 values, then rounded): warp 0.
 // Returns false if S32 is not positive definite.
-template <int M>
-__device__ bool warp_hpd_factor(WarpLAT<double>& la, const double2 (*S)[kMaxM], float2 (*S32)[M],
+template <int M, int R>
+__device__ bool warp_hpd_factor(WarpLAT<double, R>& la, const double2 (*S)[kMaxM], float2 (*S32)[M],
                                 float2 (*K)[M], int lane) {
   for (int e = lane; e < M * M; e += 32) {
     const int i = e / M, j = e % M;
@@ -56,12 +64,310 @@ __device__ bool warp_hpd_factor(WarpLAT<double>& la, const double2 (*S)[kMaxM], 
   return true;
 }
 
-__host__ __device__ constexpr int conv_min_blocks(int M) { return M <= 3 ? 4 : (M <= 4 ? 3 : 2); }
+// Lanes per time-frequency point in the lane-group pass (a power of two >= M).
+__host__ __device__ constexpr int conv_group(int M) { return M <= 4 ? 4 : 8; }
+// The layout FCA_CONV_AUTO takes for M: one thread per point at every M. Measured on GB300
+// (fused kernel, L = 50 or 100): M = 4, F = 513, N = 1000: 2.1 ms per thread vs 7.4 ms in lane
+// groups; M = 6, F = 257, N = 2000: 5.8 vs 26.2 ms; M = 8, F = 1025, N = 4000 (FP16): 401 vs
+// 546 ms. The one-thread layout's spills (200 bytes per thread at M = 6, 1.2 KB at M = 8) cost
+// less than the lane groups' exchanges and duplicated triangular work.
+__host__ __device__ constexpr bool conv_grouped(int) { return false; }
+
+// Per-group shared tiles of the lane-group pass: L^-1 (lower triangle), B = L^-1 S2, and the
+// vectors y, w = L^-1 y, u = Rx^-1 y, mu_1, mu_2 of the group's current point. The groups of a
+// warp read their own tiles at the same offsets at once: each tile's stride is padded by one
+// float2 so that those reads fall in different banks.
+template <int M, int NT>
+struct ConvGroupTiles {
+  static constexpr int NG = NT / conv_group(M);
+  struct Tile {
+    float2 Li[M][M];
+    float2 pad0;
+    float2 B[M][M];
+    float2 pad1;
+    float2 y[M], w[M], u[M], mu1[M], mu2[M];
+    float2 pad2;
+  };
+  Tile g[NG];
+};
+struct ConvNoTiles {};
+
+// Sum over the G lanes of a group (every lane of the group receives it).
+template <int G>
+__device__ __forceinline__ float group_sum(float x) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Per-lane partial sums of the lane-group pass: row r of both Gram sums (all columns; the
+// columns k >= r are used), log det Rx and y^H Rx^-1 y terms.
+template <int M>
+struct ConvGroupAcc {
+  float2 g1[M], g2[M];
+  float ld, quad;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < M; ++k) g1[k] = g2[k] = make_float2(0.f, 0.f);
+    ld = quad = 0.f;
+  }
+  __device__ __forceinline__ void add(const ConvGroupAcc& o) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      g1[k] = cadd(g1[k], o.g1[k]);
+      g2[k] = cadd(g2[k], o.g2[k]);
+    }
+    ld += o.ld;
+    quad += o.quad;
+  }
+};
+
+// One time-frequency point (y, v1, v2) on a group of G lanes (rows r = lane mod G; rows
+// r >= M carry zeros and take part in the exchanges only). The same quantities as the
+// one-thread pass of conv_em_kernel, arranged so that each lane's work is a few independent
+// dot products: Rx = v1 S1 + v2 S2 = L L^H (right-looking, row r in registers, column j's
+// entries broadcast by shuffles), column r of L^-1, then w = L^-1 y, u = L^-H w, mu_j = v_j S_j u,
+// the v update from sums of squares (K_j^H u, column r of L^-1 K_j), and row r of
+// C = v1 v2 (L^-1 S1)^H (L^-1 S2) from column r of L^-1 S1 and the tile of L^-1 S2.
+// Returns (v1', v2') on every lane of the group; adds row r of Phi_j / v_j' to acc when `on`.
+template <int M, int G, int NT>
+__device__ float2 conv_group_point(const ConvShared<M, NT / 32>& sh, ConvGroupTiles<M, NT>& gt,
+                                   int gid, int r, int base, float2 yr, float v1, float v2, float vf,
+                                   bool on, int& bad, ConvGroupAcc<M>& acc) {
+  typename ConvGroupTiles<M, NT>::Tile& tg = gt.g[gid];
+  const bool row = r < M;
+  const int rc = row ? r : 0;
+  if (row) tg.y[r] = yr;
+  // Row r of Rx (entries k <= r), factorised in place into row r of L.
+  float2 R[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    R[k] = (row && k <= r) ? cadd(cscale(sh.S32[0][r][k], v1), cscale(sh.S32[1][r][k], v2))
+                           : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float d = __shfl_sync(0xffffffffu, R[j].x, base + j);  // pivot j (lane j's diagonal)
+    const float ij = rsqrtf(d);
+    if (r == j) {
+      bad |= !(d > 0.f);
+      if (on) acc.ld += logf(d);
+      R[j] = make_float2(d * ij, ij);  // (L_jj, 1 / L_jj)
+    } else if (r > j) {
+      R[j] = cscale(R[j], ij);  // L[r][j]
+    }
+#pragma unroll
+    for (int k = j + 1; k < M; ++k) {
+      const float2 lk = shfl2(R[j], base + k);  // L[k][j]
+      if (r >= k) R[k] = csub(R[k], cmulc(R[j], lk));
+    }
+  }
+  // Column r of L^-1: x_r = 1 / L_rr, x_i = -(sum_{r <= k < i} L[i][k] x_k) / L_ii (rows of L
+  // broadcast from their lanes).
+  {
+    float2 x[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        const float2 lik = shfl2(R[k], base + i);  // L[i][k] from lane i
+        if (k >= r) s = csub(s, cmul(lik, x[k]));
+      }
+      const float iii = __shfl_sync(0xffffffffu, R[i].y, base + i);  // 1 / L_ii
+      x[i] = (i < r) ? make_float2(0.f, 0.f) : (i == r ? make_float2(iii, 0.f) : cscale(s, iii));
+    }
+    if (row) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) tg.Li[i][r] = x[i];
+    }
+  }
+  __syncwarp();
+  // w = L^-1 y (row r), then u = L^-H w (row r).
+  float2 t = make_float2(0.f, 0.f);
+  if (row) {
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if (k <= r) t = cfma(tg.Li[r][k], tg.y[k], t);
+    tg.w[r] = t;
+  }
+  if (on && row) acc.quad += cabs2(t);
+  __syncwarp();
+  t = make_float2(0.f, 0.f);
+  if (row) {
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if (k >= r) t = cfma(cconj(tg.Li[k][r]), tg.w[k], t);
+    tg.u[r] = t;
+  }
+  __syncwarp();
+  // mu_j = v_j S_j u (row r), and (K_j^H u)_r.
+  float2 m1 = make_float2(0.f, 0.f), m2 = m1, a1 = m1, a2 = m1;
+  if (row) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const float2 uk = tg.u[k];
+      m1 = cfma(sh.S32[0][r][k], uk, m1);
+      m2 = cfma(sh.S32[1][r][k], uk, m2);
+      if (k >= r) {
+        a1 = cfma(cconj(sh.K32[0][k][r]), uk, a1);
+        a2 = cfma(cconj(sh.K32[1][k][r]), uk, a2);
+      }
+    }
+    m1 = cscale(m1, v1);
+    m2 = cscale(m2, v2);
+    tg.mu1[r] = m1;
+    tg.mu2[r] = m2;
+  }
+  // Columns r of A = L^-1 S1 and B = L^-1 S2 (B into the tile), and the squared norms of
+  // columns r of L^-1 K1 and L^-1 K2 (K_j lower triangular: rows k >= r only).
+  float2 ac[M];
+  float x1n = 0.f, x2n = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float2 sa = make_float2(0.f, 0.f), sb = sa, s1 = sa, s2 = sa;
+#pragma unroll
+    for (int k = 0; k <= i; ++k) {
+      const float2 l = tg.Li[i][k];
+      sa = cfma(l, sh.S32[0][k][rc], sa);
+      sb = cfma(l, sh.S32[1][k][rc], sb);
+      if (k >= r) {
+        s1 = cfma(l, sh.K32[0][k][rc], s1);
+        s2 = cfma(l, sh.K32[1][k][rc], s2);
+      }
+    }
+    ac[i] = sa;
+    if (row) tg.B[i][r] = sb;
+    x1n += cabs2(s1);
+    x2n += cabs2(s2);
+  }
+  // v_j' = (mu_j^H S_j^-1 mu_j + tr(S_j^-1 C)) / M (Eq. (vupdate)) from the group sums:
+  // mu_j^H S_j^-1 mu_j = v_j^2 ||K_j^H u||^2, tr(S1^-1 C) = v1 v2 ||L^-1 K2||_F^2,
+  // tr(S2^-1 C) = v1 v2 ||L^-1 K1||_F^2.
+  const float q1 = group_sum<G>(cabs2(a1)), q2 = group_sum<G>(cabs2(a2));
+  const float r2 = group_sum<G>(row ? x1n : 0.f), r1 = group_sum<G>(row ? x2n : 0.f);
+  const float v1n = fmaxf(v1 * fmaf(v1, q1, v2 * r1) * (1.f / M), vf);
+  const float v2n = fmaxf(v2 * fmaf(v2, q2, v1 * r2) * (1.f / M), vf);
+  __syncwarp();
+  // Row r of Phi_j / v_j' (columns k >= r): mu_j,r conj(mu_j,k) + C[r][k], with
+  // C[r][k] = v1 v2 sum_m conj(A[m][r]) B[m][k].
+  if (on && row) {
+    const float w1 = __fdividef(1.f, v1n), w2 = __fdividef(1.f, v2n);
+    const float v12 = v1 * v2;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if (k >= r) {
+        float2 c = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < M; ++m) c = cfma(cconj(ac[m]), tg.B[m][k], c);
+        c = cscale(c, v12);
+        const float2 z1 = cadd(cmulc(m1, tg.mu1[k]), c);
+        const float2 z2 = cadd(cmulc(m2, tg.mu2[k]), c);
+        acc.g1[k] = make_float2(fmaf(z1.x, w1, acc.g1[k].x), fmaf(z1.y, w1, acc.g1[k].y));
+        acc.g2[k] = make_float2(fmaf(z2.x, w2, acc.g2[k].x), fmaf(z2.y, w2, acc.g2[k].y));
+      }
+    }
+  }
+  __syncwarp();
+  return make_float2(v1n, v2n);
+}
+
+// One iteration's pass over the bin's frames on lane groups, ending with the warp's partial
+// sums in sh.red[warp] (the layout of warp_reduce_store: diagonal, then the (re, im) pairs of
+// the upper triangle, for each Gram; then log det Rx and y^H Rx^-1 y). The point loop runs
+// the same number of times on every group (groups past the last frame compute on a dummy
+// point and add nothing).
+template <int M, int ST, int NT, bool kB>
+__device__ void conv_group_iteration(ConvShared<M, NT / 32>& sh, ConvGroupTiles<M, NT>& gt,
+                                     const ConvEmArgs& a, const typename Elem<ST>::T* ysrc, float* v1p,
+                                     float* v2p, float* vg1, int dv2, ptrdiff_t d_prev, int f, int N,
+                                     float vf, float gi, bool last, int& bad, int tid) {
+  constexpr int G = conv_group(M), P = NT / G, MM = M * M;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int gid = tid / G, r = lane & (G - 1), base = lane & ~(G - 1);
+  // Two-level FP32 sums (a block of 16 points, then the blocks), so that no FP32 sum runs over
+  // more than a few dozen terms however many frames a group takes.
+  ConvGroupAcc<M> acc, blk;
+  acc.zero();
+  blk.zero();
+  int nb = 0;
+  for (int n0 = 0; n0 < N; n0 += P) {
+    const int n = n0 + gid;
+    const bool on = n < N;
+    float2 yr = make_float2(0.f, 0.f);
+    float v1 = 1.f, v2 = 1.f;
+    if (on) {
+      v1 = v1p[n];
+      v2 = v2p[n];
+      if (r < M) yr = cscale(decode(ysrc[(size_t)n * M + r]), gi);
+      if (last && r == 0) {
+        if constexpr (kB) {
+          vg1[d_prev + n] = v1;
+          vg1[d_prev + dv2 + n] = v2;
+        } else {
+          a.v_prev[(size_t)f * N + n] = v1;
+          a.v_prev[(size_t)a.F * N + (size_t)f * N + n] = v2;
+        }
+      }
+    }
+    const float2 vn = conv_group_point<M, G, NT>(sh, gt, gid, r, base, yr, v1, v2, vf, on, bad, blk);
+    if (on && r == 0) {
+      v1p[n] = vn.x;
+      v2p[n] = vn.y;
+    }
+    if (++nb == 16) {
+      acc.add(blk);
+      blk.zero();
+      nb = 0;
+    }
+  }
+  acc.add(blk);
+  // Sum each row over the warp's groups, then write the packed partial sums.
+#pragma unroll
+  for (int o = G; o < 32; o <<= 1) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      acc.g1[k].x += __shfl_xor_sync(0xffffffffu, acc.g1[k].x, o);
+      acc.g1[k].y += __shfl_xor_sync(0xffffffffu, acc.g1[k].y, o);
+      acc.g2[k].x += __shfl_xor_sync(0xffffffffu, acc.g2[k].x, o);
+      acc.g2[k].y += __shfl_xor_sync(0xffffffffu, acc.g2[k].y, o);
+    }
+    acc.ld += __shfl_xor_sync(0xffffffffu, acc.ld, o);
+    acc.quad += __shfl_xor_sync(0xffffffffu, acc.quad, o);
+  }
+  const float ld = group_sum<G>(acc.ld), quad = group_sum<G>(acc.quad);
+  float* out = sh.red[warp];
+  if (lane < M) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if (k == lane) {
+        out[lane] = acc.g1[k].x;
+        out[MM + lane] = acc.g2[k].x;
+      } else if (k > lane) {
+        const int o = M + 2 * cpair_index(M, lane, k);
+        out[o] = acc.g1[k].x;
+        out[o + 1] = acc.g1[k].y;
+        out[MM + o] = acc.g2[k].x;
+        out[MM + o + 1] = acc.g2[k].y;
+      }
+    }
+  }
+  if (lane == 0) {
+    out[2 * MM] = ld;
+    out[2 * MM + 1] = quad;
+  }
+}
+
+// Resident CTAs per SM the register budget is sized for (kB: batches; LG: lane groups). The
+// lane-group pass spills at no M; the one-thread pass holds every per-point matrix in registers
+// and spills for M >= 6.
+__host__ __device__ constexpr int conv_min_blocks(int M, bool kB, bool LG) {
+  return LG ? (M <= 3 ? 4 : ((M == 7 || (M == 8 && kB)) ? 2 : 3)) : (M <= 3 ? 4 : (M <= 4 ? 3 : 2));
+}
 
 // kB: the CTA's bin comes from the descriptor table a.bins (a batch); otherwise bin
 // f = blockIdx.x of one mixture with v_in == v and S_in == S.
-template <int M, int ST, int NT, bool kB>
-__global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const ConvEmArgs a) {
+template <int M, int ST, int NT, bool kB, bool LG>
+__global__ void __launch_bounds__(NT, conv_min_blocks(M, kB, LG)) conv_em_kernel(const ConvEmArgs a) {
   using E = typename Elem<ST>::T;
   constexpr int NW = NT / 32;
   using Sh = ConvShared<M, NW>;
@@ -69,6 +375,7 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
   using RS = RedShape<V>;
   constexpr int MM = M * M;
   __shared__ Sh sh;
+  __shared__ typename std::conditional<LG, ConvGroupTiles<M, NT>, ConvNoTiles>::type gt;
   extern __shared__ __align__(16) unsigned char dyn[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -153,10 +460,14 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
     __syncthreads();
     if (sh.fail) break;
 
+    int bad = 0;
+    if constexpr (LG) {
+      conv_group_iteration<M, ST, NT, kB>(sh, gt, a, ysrc, v1p, v2p, vg1, dv2, d_prev, f, N, vf, gi, last,
+                                          bad, tid);
+    } else {
     float acc[RS::NA];
 #pragma unroll
     for (int j = 0; j < RS::NA; ++j) acc[j] = 0.f;
-    int bad = 0;
     for (int n = tid; n < N; n += NT) {
       float2 yv[M];
       load_bin<M, ST>(ysrc + (size_t)n * M, yv);
@@ -307,14 +618,14 @@ __global__ void __launch_bounds__(NT, conv_min_blocks(M)) conv_em_kernel(const C
       acc[2 * MM] += lp.log();
       acc[2 * MM + 1] += quad;
     }
+    warp_reduce_store<V>(acc, lane, sh.red[warp]);
+    }
     if (__syncthreads_or(bad)) {
       if (tid == 0) {
         set_status(a.status, kErrNotPD);
         sh.fail = kErrNotPD;
       }
     }
-
-    warp_reduce_store<V>(acc, lane, sh.red[warp]);
     __syncthreads();
     for (int i = tid; i < V; i += NT) {  // fixed-order FP64 merge across warps (pairwise)
       double s[NW];
@@ -454,7 +765,9 @@ static cudaError_t launch_conv_t(const ConvEmArgs& a, cudaStream_t st) {
   const int grid = a.bins ? a.nbins : a.F;
   if (grid <= 0) return cudaSuccess;
   if (a.bins && ST != 0) return cudaErrorInvalidValue;  // batches hold complex64 mixtures
-  auto k = a.bins ? conv_em_kernel<M, 0, NT, true> : conv_em_kernel<M, ST, NT, false>;
+  const bool lg = a.layout == FCA_CONV_GROUP || (a.layout != FCA_CONV_THREAD && conv_grouped(M));
+  auto k = a.bins ? (lg ? conv_em_kernel<M, 0, NT, true, true> : conv_em_kernel<M, 0, NT, true, false>)
+                  : (lg ? conv_em_kernel<M, ST, NT, false, true> : conv_em_kernel<M, ST, NT, false, false>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;

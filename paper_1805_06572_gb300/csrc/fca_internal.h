@@ -71,6 +71,7 @@ struct ConvEmArgs {
   double2* S_prev;          // [2][F][M][M] out
   double* llf;              // [iters][F]
   int* status;
+  int layout;               // FCA_CONV_AUTO / _THREAD / _GROUP (fca.h)
 };
 
 // Posterior-mean outputs.

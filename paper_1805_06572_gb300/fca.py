@@ -22,6 +22,7 @@ FCA_SEP_ALG1, FCA_SEP_FINAL_PARAMS = 0, 1
 FCA_FORM_FAST, FCA_FORM_CONVENTIONAL = 0, 1
 FCA_GEVD_FP32, FCA_GEVD_FP64, FCA_GEVD_REFINED = 0, 1, 2
 FCA_GEVD_DEFAULT = FCA_GEVD_REFINED
+FCA_CONV_AUTO, FCA_CONV_THREAD, FCA_CONV_GROUP = 0, 1, 2
 FCA_MAX_SWEEPS_LIMIT = 1000
 STATUS_NAMES = {0: "FCA_OK", 1: "FCA_ERR_ARG", 2: "FCA_ERR_CUDA", 3: "FCA_ERR_NOMEM",
                 4: "FCA_ERR_NOT_PD", 5: "FCA_ERR_EIG_NOCONV", 6: "FCA_ERR_NONFINITE",
@@ -39,7 +40,7 @@ EXPORTS = ("fca_init", "fca_load", "fca_em_conventional", "fca_em_fast", "fca_em
            "fca_batch_free",
            "fca_server_create", "fca_server_request_bytes", "fca_server_submit",
            "fca_server_wait", "fca_server_stats", "fca_server_destroy", "fca_stft_frames",
-           "fca_stft", "fca_istft")
+           "fca_stft", "fca_istft", "fca_set_conv_layout")
 
 
 class fca_problem(ctypes.Structure):
@@ -95,6 +96,7 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fca_load.argtypes = [V, ctypes.POINTER(fca_problem), V]
     lib.fca_em_conventional.argtypes = [V, I, V, V]
     lib.fca_em_fast.argtypes = [V, I, V, V]
+    lib.fca_set_conv_layout.argtypes = [V, I]
     lib.fca_em_fast_recover.argtypes = [V, I, V, V]
     lib.fca_separate.argtypes = [V, V, V, I, V]
     lib.fca_get_params.argtypes = [V, V, V, V]
@@ -242,6 +244,11 @@ def fca_load(state: State, y, v0=None, S0=None, y_scale=None, stream=None, seed=
     p = _problem(y, v0, S0, y_scale, seed, encode_f16)
     _check(lib.fca_load(ctypes.c_void_p(state.handle), ctypes.byref(p), ctypes.c_void_p(_stream(stream))),
            "fca_load")
+
+
+def fca_set_conv_layout(state: State, layout: int):
+    """FCA_CONV_AUTO, FCA_CONV_THREAD or FCA_CONV_GROUP for the state's conventional EM."""
+    _check(lib.fca_set_conv_layout(ctypes.c_void_p(state.handle), int(layout)), "fca_set_conv_layout")
 
 
 def fca_em_fast(state: State, iters: int, loglik=None, stream=None):
