@@ -118,6 +118,98 @@ __device__ void gevd_bin(const double2* S, double2* S_copy, int F, int f, double
   if (lane == 0) logdetS2[f] = -ldQ;  // P = Q: log det S2 = -log|det P|^2
 }
 
+// Workspace of gevd_bin_refined (one warp).
+template <int M>
+struct RefinedGevdWork {
+  RefineWork<M> rf;
+  WarpLAT<float, M> la;
+  float2 Xh[M][kMaxM], Xl[M][kMaxM];
+  float2 U[M][kMaxM];
+  float lh[kMaxM], ll[kMaxM];
+};
+
+// One warp, refined precision (FCA_GEVD_REFINED): the same outputs as gevd_bin from the FP32
+// solver on (S1, S2) rounded to FP32, refined against the FP64 pair (warp_refine_gevd: one
+// compensated FP32 step, a second FP64 step after a poor start); P = Xh + Xl, Lambda = lh + ll,
+// and log det S2 from an FP64 Cholesky factorisation of S2 (P^H S2 P = I).
+template <int M>
+__device__ void gevd_bin_refined(const double2* S, double2* S_copy, int F, int f, double2* P, double* lam,
+                                 double* logdetS2, int* status, RefinedGevdWork<M>& w, int max_sweeps,
+                                 int lane) {
+  const size_t MM = (size_t)M * M;
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, k = e % M;
+    const double2 s1 = S[(size_t)f * MM + e], s2 = S[((size_t)F + f) * MM + e];
+    if (S_copy) {
+      S_copy[(size_t)f * MM + e] = s1;
+      S_copy[((size_t)F + f) * MM + e] = s2;
+    }
+    w.rf.A[i][k] = s1;
+    w.rf.B[i][k] = s2;
+    split2(s1, w.rf.Ah[i][k], w.rf.Al[i][k]);
+    split2(s2, w.rf.Bh[i][k], w.rf.Bl[i][k]);
+    w.la.A[i][k] = w.rf.Ah[i][k];
+    w.la.L[i][k] = w.rf.Bh[i][k];
+  }
+  __syncwarp();
+  float ldL = 0.f;
+  int rc;
+  if constexpr (M <= 4) {
+    rc = warp_gevd_reg<M, float>(w.la.A, w.la.L, w.rf.sig0, w.rf.X0, w.U, &ldL, Prec<float>::kTol,
+                                 max_sweeps, lane);
+  } else {
+    rc = warp_gevd_fast<M, float>(w.la, lane, w.rf.sig0, w.rf.X0, w.U, &ldL, max_sweeps);
+  }
+  __syncwarp();
+  if (rc == kOk) {
+    const RefineOut out{w.Xh, w.Xl, w.lh, w.ll};
+    warp_refine_gevd<M>(w.rf, w.rf.X0, w.la.Z, w.la.A2, w.la.V2, w.la.V, w.la.L, out, lane);
+    if (lane < M) {
+      const float l = w.lh[lane];
+      if (!(l > 0.f) || !(l < Prec<float>::kHuge)) rc = kErrNotPD;
+    }
+    rc = __reduce_max_sync(0xffffffffu, rc);
+  }
+  if (rc != kOk) {
+    if (lane == 0) set_status(status, rc);
+    return;
+  }
+  for (int e = lane; e < M * M; e += 32) {
+    const float2 hi = w.Xh[e / M][e % M], lo = w.Xl[e / M][e % M];
+    P[(size_t)f * MM + e] = make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+  }
+  if (lane < M) lam[(size_t)f * M + lane] = (double)w.lh[lane] + (double)w.ll[lane];
+  if (lane == 0) {  // log det S2 = sum_k log L_kk^2, S2 = L L^H (FP64, in place in rf.B)
+    double ld = 0.0;
+    bool ok = true;
+    for (int k = 0; k < M; ++k) {
+      double d = w.rf.B[k][k].x;
+      for (int m = 0; m < k; ++m) d -= w.rf.B[k][m].x * w.rf.B[k][m].x + w.rf.B[k][m].y * w.rf.B[k][m].y;
+      ok = ok && d > 0.0;
+      const double ik = 1.0 / sqrt(d);
+      ld += log(d);
+      for (int i = k + 1; i < M; ++i) {
+        double2 s = w.rf.B[i][k];
+        for (int m = 0; m < k; ++m) s = csub(s, cmulc(w.rf.B[i][m], w.rf.B[k][m]));
+        w.rf.B[i][k] = make_double2(s.x * ik, s.y * ik);
+      }
+    }
+    if (ok) logdetS2[f] = ld;
+    else set_status(status, kErrNotPD);
+  }
+}
+
+constexpr int kRefinedWarps = 2;  // bins per CTA of gevd_from_S_refined_kernel (shared workspace)
+
+template <int M>
+__global__ void __launch_bounds__(32 * kRefinedWarps) gevd_from_S_refined_kernel(const ParamArgs a) {
+  __shared__ RefinedGevdWork<M> w[kRefinedWarps];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kRefinedWarps + wi;
+  if (f >= a.F) return;  // whole warp leaves together
+  gevd_bin_refined<M>(a.S, nullptr, a.F, f, a.P, a.lam, a.logdetS2, a.status, w[wi], a.max_sweeps, lane);
+}
+
 template <int M, typename G>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) gevd_from_S_kernel(const ParamArgs a) {
   __shared__ WarpLAT<G> la[kWarpsPerCta];
@@ -265,18 +357,24 @@ __device__ float bin_power(const typename Elem<ST>::T* yf, typename Elem<ST>::T*
 // power, the initial v clamped to it, and checks that both are finite, all on warps 1..7
 // (synchronised among themselves by named barrier 1). Warp 0 meanwhile solves the bin's
 // generalised eigenproblem when extra.S is set (PrepareExtra).
-template <int M, int ST, bool kX, typename G = float>
+template <int M, int ST, bool kX, typename G = float, bool kRefined = false>
 __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void* y, const float* ginv,
                                                       const double* v0, float* v, float* vfloor,
                                                       int* status, const BinDesc* bins,
                                                       const PrepareExtra ex) {
   using E = typename Elem<ST>::T;
   constexpr int kStreamThreads = 224;
+  struct PlainWork {
+    WarpLAT<G> la;
+    G sig[kMaxM];
+    Cx<G> Qs[kMaxM][kMaxM], Us[kMaxM][kMaxM];
+  };
+  struct NoWork {};
   __shared__ double part[8];
   __shared__ float vf_s;
-  __shared__ WarpLAT<G> la;  // used (and kept) only by the kX variants
-  __shared__ G sig[kMaxM];
-  __shared__ Cx<G> Qs[kMaxM][kMaxM], Us[kMaxM][kMaxM];
+  // the eigensolver's workspace, used only by the kX variants
+  __shared__ typename std::conditional<kX, typename std::conditional<kRefined, RefinedGevdWork<M>, PlainWork>::type,
+                                       NoWork>::type gw;
   const int tid = threadIdx.x;
   int f, N;
   size_t yoff, voff[2];
@@ -296,9 +394,13 @@ __global__ void __launch_bounds__(256) prepare_kernel(int F, int N0, const void*
   }
   int bad = 0;
   if (tid < 32) {
-    if (kX && ex.S)
-      gevd_bin<M, G>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, la, sig, Qs, Us,
-                     ex.max_sweeps, tid);
+    if constexpr (kX && kRefined) {
+      if (ex.S) gevd_bin_refined<M>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, gw, ex.max_sweeps, tid);
+    } else if constexpr (kX) {
+      if (ex.S)
+        gevd_bin<M, G>(ex.S, ex.S_copy, F, f, ex.P, ex.lam, ex.logdetS2, status, gw.la, gw.sig, gw.Qs, gw.Us,
+                       ex.max_sweeps, tid);
+    }
   } else {
     const int t = tid - 32;
     E* yc = (kX && ex.y_copy) ? reinterpret_cast<E*>(ex.y_copy) + yoff : nullptr;
@@ -398,6 +500,10 @@ __global__ void invert_scale_kernel(int F, const float* g, float* ginv) {
 cudaError_t launch_gevd_from_S(int M, const ParamArgs& a, cudaStream_t st) {
   const int grid = (a.F + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid <= 0) return cudaSuccess;
+  if (a.gevd_mode == 2) {
+    const int gr = (a.F + kRefinedWarps - 1) / kRefinedWarps;
+    FCA_DISPATCH_M(M, (gevd_from_S_refined_kernel<kM><<<gr, 32 * kRefinedWarps, 0, st>>>(a)); return cudaGetLastError())
+  }
   if (a.gevd_mode) {
     FCA_DISPATCH_M(M, (gevd_from_S_kernel<kM, double><<<grid, 32 * kWarpsPerCta, 0, st>>>(a)); return cudaGetLastError())
   }
@@ -422,6 +528,13 @@ cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, cons
   if (F <= 0) return cudaSuccess;
   if (extra && bins) return cudaErrorInvalidValue;  // the fused work assumes the [F][N][M] layout
   const PrepareExtra ex = extra ? *extra : PrepareExtra{};
+  if (extra && ex.gevd_mode == 2) {
+    if (storage) {
+      FCA_DISPATCH_M(M, (prepare_kernel<kM, 1, true, float, true><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
+    } else {
+      FCA_DISPATCH_M(M, (prepare_kernel<kM, 0, true, float, true><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())
+    }
+  }
   if (extra && ex.gevd_mode) {
     if (storage) {
       FCA_DISPATCH_M(M, (prepare_kernel<kM, 1, true, double><<<F, 256, 0, st>>>(F, N, y, ginv, v0, v, vfloor, status, bins, ex)); return cudaGetLastError())

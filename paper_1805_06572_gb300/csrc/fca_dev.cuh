@@ -1010,7 +1010,8 @@ __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], 
         const C c2 = mkc<T>(fmaT(li, r[t].x, sv[t].x), fmaT(li, r[t].y, sv[t].y));
         const T cm = maxT(absT(c1.x) + absT(c1.y), absT(c2.x) + absT(c2.y));
         C eij, eji;
-        if (cm <= T(0.1) * absT(gap)) {
+        const bool sep = cm <= T(0.1) * absT(gap) && gap != T(0);
+        if (sep) {
           const T rg = rcp_fast(gap);
           eij = mkc<T>(c1.x * rg, c1.y * rg);
           eji = mkc<T>(-c2.x * rg, c2.y * rg);
@@ -1021,7 +1022,7 @@ __device__ T warp_newton_step(const Cx<T> (*A)[kMaxM], const Cx<T> (*B)[kMaxM], 
         T1[i][j] = eij;
         T1[j][i] = eji;
         m = maxT(absT(eij.x) + absT(eij.y), absT(eji.x) + absT(eji.y));
-        if (!(cm <= T(0.1) * absT(gap)) && !(cm <= kSep * maxT(absT(li), absT(lj)))) m = T(INFINITY);
+        if (!sep && !(cm <= kSep * maxT(absT(li), absT(lj)))) m = T(INFINITY);
       }
       emax = (m > emax || m != m) ? m : emax;
     }
@@ -1155,7 +1156,7 @@ __device__ __forceinline__ float refine_pair(double li, double lj, double2 r, do
   const float c2x = (float)fma(li, r.x, s.x), c2y = (float)fma(li, r.y, s.y);
   const float cm = fmaxf(fabsf(c1x) + fabsf(c1y), fabsf(c2x) + fabsf(c2y));
   const float g = (float)gap;
-  if (cm <= (float)kRefineSep * fabsf(g)) {
+  if (cm <= (float)kRefineSep * fabsf(g) && g != 0.f) {  // (an exactly degenerate pair: r / 2)
     const float rg = __fdividef(1.f, g);
     *eij = make_float2(c1x * rg, c1y * rg);
     *eji = make_float2(-c2x * rg, c2y * rg);
@@ -1314,7 +1315,7 @@ __device__ __forceinline__ float refine_pair32(float lhi, float lli, float lhj, 
   const float c1x = fmaf(lhj, r.x, s.x), c1y = fmaf(lhj, r.y, s.y);
   const float c2x = fmaf(lhi, r.x, s.x), c2y = fmaf(lhi, r.y, s.y);
   const float cm = fmaxf(fabsf(c1x) + fabsf(c1y), fabsf(c2x) + fabsf(c2y));
-  if (cm <= (float)kRefineSep * fabsf(g)) {
+  if (cm <= (float)kRefineSep * fabsf(g) && g != 0.f) {  // (an exactly degenerate pair: r / 2)
     const float rg = __fdividef(1.f, g);
     *eij = make_float2(c1x * rg, c1y * rg);
     *eji = make_float2(-c2x * rg, c2y * rg);

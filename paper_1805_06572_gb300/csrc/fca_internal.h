@@ -114,7 +114,7 @@ struct ParamArgs {
   float* lam32;             // [F][M]
   int* status;
   int max_sweeps;           // gevd_from_S: Jacobi sweep cap
-  int gevd_mode;            // gevd_from_S: 0 = FP32 eigensolver, else FP64
+  int gevd_mode;            // gevd_from_S: FCA_GEVD_* (0 FP32, 1 FP64, 2 refined)
 };
 
 // Fused EM kernels. FastFCA: threads per CTA 128 for one mixture; 64, 128 or 256 for a
@@ -146,7 +146,7 @@ struct PrepareExtra {
   double* lam;
   double* logdetS2;
   int max_sweeps;           // Jacobi sweep cap of the eigensolver
-  int gevd_mode;            // 0: FP32 eigensolver, else FP64
+  int gevd_mode;            // FCA_GEVD_* (0 FP32, 1 FP64, 2 refined)
 };
 cudaError_t launch_prepare(int M, int storage, int F, int N, const void* y, const float* ginv,
                            const double* v0, float* v, float* vfloor, int* status,
