@@ -29,7 +29,6 @@ from __future__ import annotations
 
 import argparse
 import datetime
-import hashlib
 import json
 import os
 import statistics
@@ -80,16 +79,11 @@ def hbm_peak():
         return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
-def source_sha() -> str:
-    h = hashlib.sha256()
-    for f in ("fca_fast.cuh", "fca_dev.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1805_06572_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:12]
-
-
 def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the machine-written profiles/dram_traffic.json,
-    if it was captured at the current kernel source; else None."""
+    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.json (written by
+    paper_1805_06572_gb300.ncu_traffic from an Nsight Compute capture), if it was captured at
+    the current kernel source; else None."""
+    from paper_1805_06572_gb300.ncu_traffic import source_sha
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[kernel]
     except (OSError, ValueError, KeyError):
