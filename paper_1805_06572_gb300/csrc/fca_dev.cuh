@@ -5,15 +5,17 @@
 //     complete warp sums (31 shuffles for 32 values instead of 160 for a butterfly each);
 //   * dense Hermitian linear algebra for one frequency bin inside one warp (M <= 8):
 //     Cholesky, triangular solves, cyclic Jacobi with the round-robin (parallel) ordering,
-//     used for the generalised eigenproblem of Eq. (GEVD) on the FP32 pipe, plus FP64
-//     matrix products for the basis update P <- P Q (Eq. (updatePeff)).
+//     used for the generalised eigenproblem of Eq. (GEVD) in FP32 or FP64, plus FP64
+//     matrix products for the basis update P <- P Q (Eq. (updatePeff));
+//   * Newton-type steps for the generalised eigenbasis and their refinement with compensated
+//     FP32 arithmetic (error-free transformations, Dot2) against FP64 pencils.
 //
-// Why the eigensolver runs on the FP32 pipe: on GB300 an FP64 FMA has ~64 cycles of
-// latency, FP64 division and square root ~650 cycles, and FP64 throughput is 1/62 of FP32
-// (measured). A Jacobi sweep is a chain of dependent rotations, so an FP64 solver would
-// cost more than the whole per-bin pass of an EM iteration. FP64 is kept where the sums are
-// long or the product chain is long: the cross-warp merge of the Gram and log-likelihood
-// partial sums, and the accumulated basis P.
+// Precision: on GB300 an FP64 FMA occupies a scheduler's FP64 pipe for ~64 cycles and FP64
+// throughput is 1/74 of FP32 (measured), so a Jacobi solve in FP64 costs several times the
+// per-bin pass of an EM iteration. The library's default (refined) eigensolver therefore runs
+// FP32 steps and refines them with compensated FP32 arithmetic against the FP64-merged Grams,
+// which reaches the FP64 solver's accuracy; FP64 stays where sums or product chains are long:
+// the cross-warp merge of the Gram and log-likelihood partial sums, and the basis P.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
