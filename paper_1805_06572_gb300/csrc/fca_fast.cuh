@@ -361,7 +361,7 @@ __device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool las
     //   c_i / v_j' = (v1 v2 / v_j') t_i                 (Eq. (updatePhitildeeff))
     float r[M], tt[M], pp[M];
     float sA = 0.f, sB = 0.f, sC = 0.f, sD = 0.f, ql = 0.f;
-    LogProd lp;
+    float lg2 = 0.f;  // sum_i log2 d_i (hardware log2 per factor)
 #pragma unroll
     for (int i = 0; i < M; ++i) {
       const float d = fmaf(v1, lamr[i], v2);
@@ -375,7 +375,7 @@ __device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool las
       sC += qq;
       sD += tt[i];
       ql += pr;
-      lp.mul(d);
+      lg2 += __log2f(d);
     }
     const float v1n = fmaxf((v1 * (1.f / M)) * fmaf(v1, sA, v2 * sB), vf);
     const float v2n = fmaxf((v2 * (1.f / M)) * fmaf(v2, sC, v1 * sD), vf);
@@ -407,7 +407,7 @@ __device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool las
           acc[o] = fmaf(w, z.x, acc[o]);
           acc[o + 1] = fmaf(w, z.y, acc[o + 1]);
         }
-      acc[MM] += q ? 0.f : lp.log_fast();
+      acc[MM] += q ? 0.f : 0.6931471805599453f * lg2;
       acc[MM + 1] += q ? 0.f : ql;
     } else {
       float s1[M], s2[M];
@@ -430,7 +430,7 @@ __device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool las
           acc[MM + o] = fmaf(w2, z.x, acc[MM + o]);
           acc[MM + o + 1] = fmaf(w2, z.y, acc[MM + o + 1]);
         }
-      acc[2 * MM] += lp.log_fast();
+      acc[2 * MM] += 0.6931471805599453f * lg2;
       acc[2 * MM + 1] += ql;
     }
   }
