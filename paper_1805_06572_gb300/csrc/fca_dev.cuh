@@ -1127,8 +1127,8 @@ __device__ __forceinline__ void split2(double2 v, float2& hi, float2& lo) {
 // FP64 working arrays of the refined eigensolver (shared memory), for order at most R.
 template <int R = kMaxM>
 struct RefineWork {
-  double2 A[R][kMaxM];   // the pencil (A, B) in FP64, B positive definite
-  double2 B[R][kMaxM];
+  double2 A[R][kMaxM];   // the pencil (A, B) in FP64, B positive definite (in the EM kernel
+  double2 B[R][kMaxM];   //   formed from the pairs below only for the FP64 step)
   float2 Ah[R][kMaxM];   // A and B split into FP32 pairs (hi + lo)
   float2 Al[R][kMaxM];
   float2 Bh[R][kMaxM];
@@ -1480,6 +1480,11 @@ __device__ void warp_refine_gevd(RefineWork<R>& w, const float2 (*X0)[kMaxM], fl
   constexpr int MM = M * M;
   const float em = warp_refine_step_df<M>(w, X0, E, T1h, T1l, T2h, T2l, out, lane);
   if (em <= 1e-4f) return;  // (NaN goes on, and stays NaN)
+  for (int e = lane; e < MM; e += 32) {  // the FP64 pencil from its pairs
+    const int i = e / M, k = e % M;
+    w.A[i][k] = make_double2((double)w.Ah[i][k].x + (double)w.Al[i][k].x, (double)w.Ah[i][k].y + (double)w.Al[i][k].y);
+    w.B[i][k] = make_double2((double)w.Bh[i][k].x + (double)w.Bl[i][k].x, (double)w.Bh[i][k].y + (double)w.Bl[i][k].y);
+  }
   for (int e = lane; e < MM; e += 32) {
     const float2 hi = out.Xh[e / M][e % M], lo = out.Xl[e / M][e % M];
     w.X[e / M][e % M] = make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
@@ -1496,15 +1501,16 @@ __device__ void warp_refine_gevd(RefineWork<R>& w, const float2 (*X0)[kMaxM], fl
   __syncwarp();
 }
 
-// log det B of a Hermitian positive definite B near the identity (FP64, shared memory), by an
-// FP32 Cholesky factorisation on one lane written in terms of H = B - I (formed in FP64):
+// log det B of a Hermitian positive definite B near the identity (given as the FP32 pair
+// Bh + Bl in shared memory), by an FP32 Cholesky factorisation on one lane written in terms of
+// H = B - I (formed from the pair: Bh - 1 is exact for Bh near 1, then + Bl):
 // the pivots are 1 + delta_k with delta_k = H_kk - sum_{m<k} |L_km|^2 computed from small
 // quantities, and log det B = sum_k log1p(delta_k). Rounding then perturbs the result by about
 // 2^-24 |H| rather than 2^-24 (the Grams of a converging FastFCA iteration are close to the
 // identity in the current basis). Returns the value on every lane; NaN if a pivot is not
 // positive.
 template <int M>
-__device__ double warp_logdet_hpd32(const double2 (*B)[kMaxM], int lane) {
+__device__ double warp_logdet_hpd32(const float2 (*Bh)[kMaxM], const float2 (*Bl)[kMaxM], int lane) {
   double ld = 0.0;
   if (lane == 0) {
     float2 L[M][M];
@@ -1514,8 +1520,8 @@ __device__ double warp_logdet_hpd32(const double2 (*B)[kMaxM], int lane) {
     for (int j = 0; j < M; ++j) {
 #pragma unroll
       for (int i = j; i < M; ++i) {
-        const double2 bij = B[i][j];
-        float2 s = make_float2((float)(i == j ? bij.x - 1.0 : bij.x), (float)bij.y);
+        const float2 bh = Bh[i][j], bl = Bl[i][j];  // B = Bh + Bl; Bh - 1 is exact near 1
+        float2 s = make_float2((i == j ? bh.x - 1.f : bh.x) + bl.x, bh.y + bl.y);
 #pragma unroll
         for (int k = 0; k < j; ++k) s = csub(s, cmulc(L[i][k], L[j][k]));
         if (i == j) {

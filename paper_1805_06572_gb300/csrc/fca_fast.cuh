@@ -35,8 +35,8 @@ namespace fca {
 // Precision modes of the per-bin generalised eigenproblem (FCA_GEVD_* in fca.h):
 //   0  FP32 merge of the Gram partials, FP32 Cholesky + Jacobi, FP32 Q;
 //   1  FP64 merge, FP64 Cholesky + Jacobi, FP64 Q;
-//   2  FP64 merge, FP32 Newton-type iteration (or Cholesky + Jacobi), one refinement step of
-//      Q with compensated FP32 residuals (a second, FP64 step after a poor start); Q and Sigma
+//   2  compensated FP32 merge (pairs), FP32 Newton-type iteration (or Cholesky + Jacobi), one
+//      refinement step of Q with compensated FP32 residuals (a second, FP64 step after a poor start); Q and Sigma
 //      as FP32 pairs, made FP64 by the deferred bookkeeping.
 template <int GM> struct GevdTypes;
 template <> struct GevdTypes<0> { using Merge = float; using Solve = float; using Out = float; };
@@ -219,11 +219,11 @@ __device__ void fast_deferred_ll(Sh& sh, const FastEmArgs& a, int f, int N, int 
 }
 
 // Refined mode, log-likelihood warp: the basis Q of iteration it is St2-orthonormal, so
-// log|det Q|^2 = -log det St2 (from the FP64 Gram, read-only during the tail).
+// log|det Q|^2 = -log det St2 (from the merged Gram's pair, read-only during the tail).
 template <int M, int GM, typename Sh>
 __device__ void fast_logdet(Sh& sh, FastWork<M, GM>& w, int it, int lane) {
   if constexpr (GM == 2) {
-    const double ld = warp_logdet_hpd32<M>(w.rf.B, lane);
+    const double ld = warp_logdet_hpd32<M>(w.rf.Bh, w.rf.Bl, lane);
     if (lane == 0) sh.ldL[it & 1] = -ld;
   }
 }
@@ -441,10 +441,11 @@ __device__ void fast_pass(Sh& sh, const BinIO<ST>& io, int t, int nthr, bool las
   }
 }
 
-// Merge the NWR warp partials of a bin in a fixed order (pairwise): Gram entries in the
-// eigensolver's merge precision (FP32 sums, or the FP32 warp partials summed in FP64) into the
-// solver's work matrices, the two log-likelihood sums with a compensated two-float sum kept in
-// FP64 into llt[b]. Threads t < nthr of the caller's, one value per thread.
+// Merge the NWR warp partials of a bin in a fixed order: Gram entries in the eigensolver's
+// merge precision (FP32 sums; the FP32 warp partials summed in FP64; or, refined mode, summed
+// as compensated FP32 pairs) into the solver's work matrices, the two log-likelihood sums with
+// a compensated two-float sum kept in FP64 into llt[b]. Threads t < nthr of the caller's, one
+// value per thread.
 template <int M, int NWR, int GM, typename Sh>
 __device__ void fast_merge(Sh& sh, FastWork<M, GM>& w, int b, double invN, int t, int nthr) {
   using MT = typename GevdTypes<GM>::Merge;
@@ -452,7 +453,30 @@ __device__ void fast_merge(Sh& sh, FastWork<M, GM>& w, int b, double invN, int t
   constexpr int MM = M * M;
   constexpr int V = 2 * MM + 2;
   for (int e = t; e < V; e += nthr) {
-    if (e < 2 * MM) {
+    if (GM == 2 && e < 2 * MM) {
+      // Refined mode: the warp partials summed as an unevaluated FP32 pair (TwoSum), scaled by
+      // 1/N given as a pair (TwoProduct): hi + lo carries the merged Gram entry to about 2^-48,
+      // as the refinement step needs, on the FP32 pipe; hi is the FP32 solver's copy.
+      float hi = sh.red[0][e], lo = 0.f;
+#pragma unroll
+      for (int k = 1; k < NWR; ++k) {
+        float err;
+        two_sum(hi, sh.red[k][e], hi, err);
+        lo += err;
+      }
+      const float ih = (float)invN, il = (float)(invN - (double)ih);
+      const float p = hi * ih;
+      const float pe = fmaf(hi, ih, -p);
+      float h, l;
+      two_sum(p, fmaf(hi, il, fmaf(lo, ih, pe)), h, l);
+      int g, i, k, part;
+      value_entry<M>(e, &g, &i, &k, &part);
+      merge_store<M>(g ? w.la.L : w.la.A, i, k, part, h);
+      if constexpr (GM == 2) {
+        merge_store<M>(g ? w.rf.Bh : w.rf.Ah, i, k, part, h);
+        merge_store<M>(g ? w.rf.Bl : w.rf.Al, i, k, part, l);
+      }
+    } else if (e < 2 * MM) {
       MT sv[NWR];
 #pragma unroll
       for (int k = 0; k < NWR; ++k) sv[k] = (MT)sh.red[k][e];
@@ -464,13 +488,6 @@ __device__ void fast_merge(Sh& sh, FastWork<M, GM>& w, int b, double invN, int t
       int g, i, k, part;
       value_entry<M>(e, &g, &i, &k, &part);
       merge_store<M>(g ? w.la.L : w.la.A, i, k, part, (ST2)val);
-      if constexpr (GM == 2) {
-        const double dv = (double)val;
-        const float hv = (float)dv, lv = (float)(dv - (double)hv);
-        merge_store<M>(g ? w.rf.B : w.rf.A, i, k, part, dv);
-        merge_store<M>(g ? w.rf.Bh : w.rf.Ah, i, k, part, hv);
-        merge_store<M>(g ? w.rf.Bl : w.rf.Al, i, k, part, lv);
-      }
     } else {
       float hi = sh.red[0][e], lo = 0.f;
 #pragma unroll
