@@ -415,7 +415,7 @@ def run_mid(args, fca, torch, dev, peaks, clk, world, rank):
         "data": "synthetic",
         "config": {"workload": f"mid: M={M} F={F} N={N} L={L}, 2 sources, complex64, seeded mixture "
                                f"per rank (delta={c.delta}, sigma={c.sigma}), mask-based initialisation",
-                   "form": "FastFCA", "eigensolver": "refined (library default: FP64 Gram merge, "
+                   "form": "FastFCA", "eigensolver": "refined (library default: Gram merge as compensated FP32 pairs, "
                    "FP32 Newton/Jacobi solve, compensated-FP32 refinement step)",
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": f"replicas x{world}",

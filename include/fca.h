@@ -169,12 +169,12 @@ fca_status fca_sync_status(fca_state* s, void* cuda_stream);
  * feed it (Eq. (updateStildeeff)).
  *   FCA_GEVD_FP32:    both in FP32.
  *   FCA_GEVD_FP64:    both in FP64 (the per-warp partial sums over frames stay FP32).
- *   FCA_GEVD_REFINED: the merge in FP64; an FP32 solve (Newton-type steps from the
- *                     identity, or the FP32 Cholesky and Jacobi solve after a poor start),
- *                     then one refinement step of Q against the FP64-merged Grams with
- *                     compensated FP32 residuals (twice FP32's precision), and a second,
- *                     FP64 step after a poor start: Q^H St2 Q = I and Q^H St1 Q diagonal to
- *                     second order in the FP32 solve's residuals.
+ *   FCA_GEVD_REFINED: the merge as compensated FP32 pairs (about twice FP32's precision); an
+ *                     FP32 solve (Newton-type steps from the identity, or the FP32 Cholesky
+ *                     and Jacobi solve after a poor start), then one refinement step of Q
+ *                     against the merged Grams' pairs with compensated FP32 residuals, and
+ *                     a second, FP64 step after a poor start: Q^H St2 Q = I and Q^H St1 Q
+ *                     diagonal to second order in the FP32 solve's residuals.
  * In the FP64 and refined modes the next basis P Q for the bin pass is a compensated FP32
  * product of P and Q each split into two FP32 parts, accurate to FP32 in every entry. The bin
  * pass is FP32 and the basis P, log-likelihood and log det S2 are kept in FP64 in every mode.

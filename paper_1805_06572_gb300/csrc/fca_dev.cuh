@@ -13,9 +13,9 @@
 // Precision: on GB300 an FP64 FMA occupies a scheduler's FP64 pipe for ~64 cycles and FP64
 // throughput is 1/74 of FP32 (measured), so a Jacobi solve in FP64 costs several times the
 // per-bin pass of an EM iteration. The library's default (refined) eigensolver therefore runs
-// FP32 steps and refines them with compensated FP32 arithmetic against the FP64-merged Grams,
-// which reaches the FP64 solver's accuracy; FP64 stays where sums or product chains are long:
-// the cross-warp merge of the Gram and log-likelihood partial sums, and the basis P.
+// FP32 steps and refines them with compensated FP32 arithmetic against the Grams merged as
+// compensated FP32 pairs, which reaches the FP64 solver's accuracy; FP64 stays where sums or
+// product chains are long: the log-likelihood sums and the accumulated basis P.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>

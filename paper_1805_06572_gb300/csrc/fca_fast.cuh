@@ -517,7 +517,7 @@ __device__ int fast_solve(Sh& sh, FastWork<M, GM>& w, const FastEmArgs& a, int b
     // previous iteration's parameters, so the new Grams are nearly diagonal in it): FP32
     // steps until the correction is below 1e-3 (the basis then has residuals of order 1e-6,
     // which the compensated refinement step squares), then the refinement against the
-    // FP64-merged Grams. A poor start (a first correction above 0.1, or steps that do not
+    // merged Grams' pairs. A poor start (a first correction above 0.1, or steps that do not
     // converge quadratically) takes the FP32 Cholesky + Jacobi solver instead, whose basis
     // is then refined the same way.
     rc = kOk;
