@@ -383,7 +383,10 @@ void fca_batch_free(fca_batch* b);
  *
  * A server owns one device-memory arena (allocated once, at creation), a pool of CUDA streams
  * and a worker thread. Submitted requests wait in arrival order; the worker admits the oldest
- * as soon as its device memory fits in the arena and a stream is free, enqueues its whole job
+ * as soon as its device memory fits in the arena and a stream is free (while the oldest waits
+ * for memory, a later request that fits may be admitted ahead of it, at most 8 times per
+ * waiting request, so a large request neither blocks the small ones behind it nor starves),
+ * enqueues its whole job
  * on that stream (copies of the inputs to the device, the one-mixture EM kernels of Sec. 2 or
  * Sec. 3 / Algorithm 1, copies of the outputs back), and retires it when the stream's event
  * completes, returning its memory and stream to the pools. Requests admitted while others run

@@ -1,8 +1,11 @@
 // Serving: requests (one mixture each) arrive at any time, are admitted as device memory and
 // stream slots free up, and run concurrently on the GPU (fca_server_* in fca.h).
 //
-// One worker thread owns the GPU side. It admits queued requests in arrival order while the
-// head request's device memory fits in the arena and a stream slot is free, enqueues the whole
+// One worker thread owns the GPU side. It admits queued requests oldest first while a stream
+// slot is free: the oldest when its device memory fits in the arena; when it does not, a later
+// request that fits may go ahead of it, at most kMaxBypass times per waiting request (so a
+// large request waiting for room does not hold up the small ones behind it, and is not
+// starved by them). It enqueues the whole
 // job of an admitted request on its slot's stream (host-to-device copies of the inputs, the
 // one-mixture EM kernels, device-to-host copies of the outputs and of the status word, and an
 // event), and polls the events of the requests in flight. When a request's event completes its
@@ -137,7 +140,13 @@ struct Pending {
   fca_request r;
   size_t bytes;
   double t_submit;
+  int bypassed = 0;  // later requests admitted ahead of this one while it waited for memory
 };
+
+// Admission: at most this many later requests go ahead of a request waiting for memory, found
+// among the next kBypassScan requests of the queue.
+constexpr int kMaxBypass = 8;
+constexpr size_t kBypassScan = 32;
 
 struct Running {
   uint64_t ticket;
@@ -336,11 +345,23 @@ void worker_main(fca_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    // Admit in arrival order while the head fits.
+    // Admit the oldest request while it fits; while it does not, a later one that fits may go
+    // ahead of it (bounded by kMaxBypass).
     while (!s->queue.empty() && !s->free_slots.empty()) {
-      Pending& p = s->queue.front();
-      size_t off = 0;
-      if (!s->arena.alloc(p.bytes, &off)) break;
+      size_t off = 0, pick = 0;
+      if (!s->arena.alloc(s->queue.front().bytes, &off)) {
+        if (s->queue.front().bypassed >= kMaxBypass) break;
+        pick = s->queue.size();
+        for (size_t i = 1; i < s->queue.size() && i <= kBypassScan; ++i) {
+          if (s->arena.alloc(s->queue[i].bytes, &off)) {
+            pick = i;
+            break;
+          }
+        }
+        if (pick == s->queue.size()) break;
+        ++s->queue.front().bypassed;
+      }
+      const Pending p = s->queue[pick];
       Running run;
       run.ticket = p.ticket;
       run.r = p.r;
@@ -349,7 +370,7 @@ void worker_main(fca_server* s) {
       run.slot = s->free_slots.back();
       s->free_slots.pop_back();
       s->infos[p.ticket].info.t_admit = now_s();
-      s->queue.pop_front();
+      s->queue.erase(s->queue.begin() + (ptrdiff_t)pick);
       lk.unlock();
       run.launch_error = launch_request(s, run.r, s->base + off, run.slot, s->streams[run.slot]);
       lk.lock();
