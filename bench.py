@@ -94,8 +94,9 @@ def profiled_traffic(kernel: str):
 
 
 def roofline(M, units, kernel_ms, peaks, flops_fn, kernel, storage="c64", mode=None):
-    """Roofline of a fused EM kernel: the streaming HBM model (SURVEY's bound) and, next to it,
-    the FP32 ALU fraction against the FP32 FMA peak measured in this run."""
+    """Roofline of a fused EM kernel: the streaming HBM model (bytes_per_bin_iter: 48 B per
+    TF-bin-iteration at M=4) and, next to it, the FP32 ALU fraction against the FP32 FMA peak
+    measured in this run."""
     hbm, hbm_src = peaks["hbm_gbs"], peaks["hbm_src"]
     gbs = bytes_per_bin_iter(M, storage) * units / (kernel_ms / 1e3) / 1e9
     tf = flops_fn(M) * units / (kernel_ms / 1e3) / 1e12
